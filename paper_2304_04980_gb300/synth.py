@@ -1,0 +1,130 @@
+"""Seeded synthetic LQ problems on a K x N grid of coupled subsystems.
+
+This module only draws inputs: per-node dynamics blocks, cost blocks and the
+initial state.  It holds none of the solver's arithmetic, so both the CUDA
+path and the CPU oracle can be fed from it.
+
+Every array is in the library's host layout, with node index p = i*N + j
+(i: 0..K-1 vertical, j: 0..N-1 horizontal):
+
+    A_self [K*N, n, n]      A_{i,j}
+    A_nbr  [K*N, 4, n, n]   E (j-1), F (j+1), G (i-1), H (i+1)
+    B      [K*N, n, m]
+    Q      [K*N, n, n]      stage state weight (t < T)
+    R      [K*N, m, m]      stage input weight
+    Q_T    [K*N, n, n]      terminal state weight
+    x0     [K*N, n]         gamma, the initial state
+
+The dynamics these blocks define are those of the paper's grid model
+(Section II, eq. 2d_graph_dynamics); the workload shapes follow the paper's
+experiments (Section V: n = 4, m = 1..2, Q = I, R of order one).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class GridLQ:
+    K: int
+    N: int
+    T: int
+    n: int
+    m: int
+    A_self: np.ndarray
+    A_nbr: np.ndarray
+    B: np.ndarray
+    Q: np.ndarray
+    R: np.ndarray
+    Q_T: np.ndarray
+    x0: np.ndarray
+    name: str = ""
+
+    @property
+    def nodes(self) -> int:
+        return self.K * self.N
+
+    def arrays(self):
+        """The seven input arrays in argument order of lq2d_create."""
+        return (self.A_self, self.A_nbr, self.B, self.Q, self.R, self.Q_T, self.x0)
+
+    def with_x0(self, x0: np.ndarray) -> "GridLQ":
+        return dataclasses.replace(self, x0=np.ascontiguousarray(x0, dtype=np.float64))
+
+
+def _eye_blocks(count: int, size: int, scale: float) -> np.ndarray:
+    return np.broadcast_to(np.eye(size) * scale, (count, size, size)).copy()
+
+
+def random_grid(K: int, N: int, T: int, n: int, m: int, seed: int, *,
+                rho: float = 0.95, coupling: float = 0.1, r_weight: float = 0.1,
+                qT_weight: float = 10.0, name: str = "") -> GridLQ:
+    """Random heterogeneous grid (the K=N=4, T=20 workload's recipe).
+
+    Draw order from numpy's PCG64 stream: A_self for every node (node-major),
+    then A_nbr, then B, then x0.  A_self is a standard-normal n x n matrix
+    scaled so that its largest eigenvalue modulus is `rho`; each neighbour
+    block is standard normal times `coupling`; B is standard normal; Q = I,
+    R = r_weight * I, Q_T = qT_weight * I; x0 is standard normal.
+    """
+    rng = np.random.default_rng(seed)
+    nodes = K * N
+    A_self = rng.standard_normal((nodes, n, n))
+    for p in range(nodes):
+        rad = np.max(np.abs(np.linalg.eigvals(A_self[p])))
+        A_self[p] *= rho / rad
+    A_nbr = rng.standard_normal((nodes, 4, n, n)) * coupling
+    B = rng.standard_normal((nodes, n, m))
+    x0 = rng.standard_normal((nodes, n))
+    return GridLQ(K, N, T, n, m, A_self, A_nbr, B,
+                  _eye_blocks(nodes, n, 1.0), _eye_blocks(nodes, m, r_weight),
+                  _eye_blocks(nodes, n, qT_weight), x0, name=name)
+
+
+def diffusion_grid(K: int, N: int, T: int, n: int = 4, m: int = 2, seed: int = 1,
+                   name: str = "") -> GridLQ:
+    """Smooth diffusion-like grid (the K=N=64, T=100 workload's recipe).
+
+    A_self = I + 0.05 * tridiag(1, -2, 1) at every node; each neighbour block
+    is 0.05 * I plus entrywise normal noise of standard deviation 0.01;
+    B ~ N(0, 1/m) entrywise; Q = I, R = 0.01 * I, Q_T = I; x0 is a Gaussian
+    bump exp(-((i-c)^2 + (j-c)^2) / (2 sigma^2)) in every state component,
+    with 1-based i, j, c = (K+1)/2 and sigma = K/8.
+    Draw order: A_nbr noise, then B.
+    """
+    rng = np.random.default_rng(seed)
+    nodes = K * N
+    lap = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    A_self = np.broadcast_to(np.eye(n) + 0.05 * lap, (nodes, n, n)).copy()
+    A_nbr = 0.05 * np.eye(n)[None, None] + 0.01 * rng.standard_normal((nodes, 4, n, n))
+    B = rng.standard_normal((nodes, n, m)) / np.sqrt(m)
+    ii, jj = np.meshgrid(np.arange(1, K + 1), np.arange(1, N + 1), indexing="ij")
+    c_i, c_j = (K + 1) / 2.0, (N + 1) / 2.0
+    sigma = K / 8.0
+    bump = np.exp(-((ii - c_i) ** 2 + (jj - c_j) ** 2) / (2.0 * sigma ** 2)).reshape(nodes)
+    x0 = np.repeat(bump[:, None], n, axis=1)
+    return GridLQ(K, N, T, n, m, A_self, A_nbr, B,
+                  _eye_blocks(nodes, n, 1.0), _eye_blocks(nodes, m, 0.01),
+                  _eye_blocks(nodes, n, 1.0), x0, name=name)
+
+
+# The named workloads.  S = L = 2 everywhere (the paper's setting, Section V).
+WORKLOADS = {
+    "grid4_T20": dict(kind="random", K=4, N=4, T=20, n=2, m=1, seed=0, tol=1e-10),
+    "grid64_T100": dict(kind="diffusion", K=64, N=64, T=100, n=4, m=2, seed=1, tol=1e-8),
+    "grid256_T200": dict(kind="random", K=256, N=256, T=200, n=4, m=2, seed=2, tol=1e-8),
+}
+
+
+def workload(name: str) -> GridLQ:
+    w = WORKLOADS[name]
+    if w["kind"] == "random":
+        return random_grid(w["K"], w["N"], w["T"], w["n"], w["m"], w["seed"], name=name)
+    return diffusion_grid(w["K"], w["N"], w["T"], w["n"], w["m"], w["seed"], name=name)
+
+
+def random_vector(shape, seed: int) -> np.ndarray:
+    """A seeded standard-normal test vector (operator and preconditioner probes)."""
+    return np.random.default_rng(seed).standard_normal(shape)
