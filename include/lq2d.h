@@ -1,0 +1,168 @@
+/*
+ * lq2d — structured LQ optimal control over a K x N grid of coupled
+ * subsystems, solved by preconditioned conjugate gradients with the nested
+ * block-Jacobi preconditioner (Zafar & Manchester, "Structured linear
+ * quadratic control computations over 2D grids").
+ *
+ * Problem (Section II, eqs. 2d_graph_dynamics and LQ_problem): node (i, j),
+ * i = 0..K-1 (vertical), j = 0..N-1 (horizontal), state x in R^n, input u
+ * in R^m, horizon t = 0..T:
+ *   x_{i,j,t+1} = A x_{i,j,t} + B u_{i,j,t} + E x_{i,j-1,t} + F x_{i,j+1,t}
+ *                 + G x_{i-1,j,t} + H x_{i+1,j,t} (+ omega_{t}, optional)
+ *   x_{i,j,0} = gamma_{i,j};  states beyond the grid edge are zero
+ *   minimise 1/2 sum_t sum_{i,j} (x'Q x + u'R u), with Q_T at t = T, no u_T.
+ * All blocks are time-invariant; Q, R, Q_T must be symmetric positive
+ * definite.
+ *
+ * The solve reduces the KKT system to Delta delta = r_delta (Section II-B),
+ * Delta = A~ Q~^-1 A~' + B~ R~^-1 B~', r_delta = -omega~, and runs
+ * Algorithm 1 (PCGM) with S outer x L inner sweeps of Algorithm 2 (NBJM) as
+ * preconditioner (Theorem posdef_preconditioner: SPD for even L).  Then
+ * x = Q~^-1 A~' delta and u = R~^-1 B~' delta.
+ *
+ * Conventions
+ *   - Node index p = i*N + j.  All arrays are row-major FP64.
+ *   - Host-layout vectors are time-major: x and costate [T+1][K*N][n],
+ *     u [T][K*N][m].  Device entry points take device pointers in the same
+ *     layout and run on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream).
+ *   - Inputs are copied; the caller keeps ownership of every pointer.
+ *     Outputs are written only into caller buffers; any output pointer may
+ *     be NULL to skip it.
+ *   - Every call returns an lq2d status; on a non-OK status
+ *     lq2d_last_error() describes it (thread-local, valid until the next
+ *     call on the same thread).  A call that fails leaves the handle usable
+ *     unless the status is LQ2D_ECUDA.
+ *   - The library needs a CUDA GPU (sm_103a); there is no CPU fallback.
+ */
+#ifndef LQ2D_H
+#define LQ2D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lq2d_problem lq2d_problem; /* opaque, library-owned */
+
+enum {
+  LQ2D_OK = 0,
+  LQ2D_EINVAL = 1,      /* bad dimensions or arguments, non-finite input, L odd or < 2 */
+  LQ2D_ENOTPD = 2,      /* Cholesky of Q, Q_T, R or of a Phi_bar block failed */
+  LQ2D_ENOCONV = 3,     /* max_iter reached; outputs hold the last iterate */
+  LQ2D_EBREAKDOWN = 4,  /* y'd <= 0 or a non-finite scalar inside Algorithm 1 */
+  LQ2D_ECUDA = 5,       /* a CUDA call failed */
+  LQ2D_ENOMEM = 6,      /* device allocation failed */
+  LQ2D_ETIMEOUT = 7     /* the device loop hit its hard iteration cap */
+};
+
+/* Options for lq2d_set_option. */
+enum {
+  LQ2D_OPT_STOP_MODE = 1,    /* 0: stop when ||r||_2 <= tol ||r_delta||_2 (default);
+                                1: stop when ||r||_inf < tol (Algorithm 1 line 11 as printed) */
+  LQ2D_OPT_DRIVER = 2,       /* 0: the PCG loop runs on the device as a CUDA graph with a
+                                   conditional while node (default);
+                                1: the host enqueues the steps, checking the stop flag every
+                                   few steps */
+  LQ2D_OPT_TIMING = 3,       /* 1: record CUDA events around every sweep and Delta-apply launch
+                                   (forces driver 1); read the totals with lq2d_get_stats */
+  LQ2D_OPT_MAX_RESTARTS = 4  /* restarts allowed when the recurrence residual passes but the
+                                true residual does not (default 3) */
+};
+
+/* Statistics of the last solve on a handle. */
+typedef struct lq2d_stats {
+  int iterations;          /* PCG steps (loop passes of Algorithm 1) over all restarts */
+  int restarts;            /* restarts from the true residual */
+  int status;              /* status returned by the solve */
+  int sweep_launches;      /* timed sweep launches (timing option) */
+  int delta_launches;      /* timed Delta-apply launches (timing option, 2 kernels each) */
+  int pad;
+  double rel_residual;     /* ||r||_2 / ||r_delta||_2 of the recurrence residual at exit */
+  double rel_kkt_residual; /* ||KKT residual of (x, u, delta)||_2 / ||r_delta||_2 */
+  double kkt_inf;          /* max |A~x + B~u + omega~| */
+  double cost;             /* 1/2 (x'Q~x + u'R~u) */
+  double sweep_ms;         /* summed device time of the timed sweep launches */
+  double delta_ms;         /* summed device time of the timed Delta-apply launches */
+} lq2d_stats;
+
+/* Creates a problem from host arrays, copies them to the current device and
+ * factors the preconditioner (Section IV-B: one banded block-Cholesky
+ * factorisation per column pair v and time class, done once).
+ *   A_self [K*N][n][n]      A_{i,j}
+ *   A_nbr  [K*N][4][n][n]   E (j-1), F (j+1), G (i-1), H (i+1); blocks that
+ *                           point off the grid are ignored
+ *   B      [K*N][n][m]
+ *   Q, Q_T [K*N][n][n]      stage and terminal state weights (SPD)
+ *   R      [K*N][m][m]      input weight (SPD)
+ *   x0     [K*N][n]         gamma
+ * Limits: 1 <= n <= 8, 1 <= m <= 8, K, N, T >= 1.
+ * Returns LQ2D_EINVAL, LQ2D_ENOTPD, LQ2D_ENOMEM or LQ2D_ECUDA on failure
+ * (then *out is NULL). */
+int lq2d_create(lq2d_problem **out, int K, int N, int T, int n, int m,
+                const double *A_self, const double *A_nbr, const double *B,
+                const double *Q, const double *R, const double *Q_T,
+                const double *x0);
+
+/* As lq2d_create, with the seven arrays already in device memory (same
+ * layouts).  Work is ordered on `stream`; the call returns after it. */
+int lq2d_create_device(lq2d_problem **out, int K, int N, int T, int n, int m,
+                       const double *d_A_self, const double *d_A_nbr, const double *d_B,
+                       const double *d_Q, const double *d_R, const double *d_Q_T,
+                       const double *d_x0, void *stream);
+
+/* Replaces the problem data of an existing handle by new device arrays of
+ * the same sizes and re-runs the setup (inverses, splitting blocks,
+ * factorisation of Phi_bar).  Allocates nothing. */
+int lq2d_update_device(lq2d_problem *h, const double *d_A_self, const double *d_A_nbr,
+                       const double *d_B, const double *d_Q, const double *d_R,
+                       const double *d_Q_T, const double *d_x0, void *stream);
+
+/* Boundary/affine terms omega_t (Section II-A: M_hat alpha + N_hat beta),
+ * host array [T][K*N][n] entering x_{t+1} = ... + omega_t; NULL clears them. */
+int lq2d_set_affine(lq2d_problem *h, const double *w);
+
+/* Solves with host buffers (Algorithm 1 with Algorithm 2 as preconditioner).
+ *   tol        > 0; see LQ2D_OPT_STOP_MODE
+ *   outer_S    >= 1 outer sweeps; inner_L >= 2 and even (the Theorem needs even L)
+ *   max_iter   >= 0 PCG steps
+ *   delta0     NULL for delta^(0) = 0, else a warm start [T+1][K*N][n]
+ *   x [T+1][K*N][n], u [T][K*N][m], costate [T+1][K*N][n] = delta of
+ *   Delta delta = r_delta (so delta_t = -P_t x_t for the Riccati matrices P_t)
+ *   iterations, rel_kkt_residual: scalar outputs (see lq2d_stats)
+ * LQ2D_ENOCONV and LQ2D_EBREAKDOWN still write the outputs. */
+int lq2d_solve(lq2d_problem *h, double tol, int outer_S, int inner_L, int max_iter,
+               const double *delta0, double *x, double *u, double *costate,
+               int *iterations, double *rel_kkt_residual);
+
+/* As lq2d_solve with device buffers, ordered on `stream`.  Returns after
+ * the work on `stream` is complete; other streams are not synchronised. */
+int lq2d_solve_device(lq2d_problem *h, double tol, int outer_S, int inner_L, int max_iter,
+                      const void *d_delta0, void *d_x, void *d_u, void *d_costate,
+                      int *iterations, double *rel_kkt_residual, void *stream);
+
+/* y = Delta d (Section II-B, the product of Algorithm 1 line 7), device
+ * buffers [T+1][K*N][n].  Returns after the work on `stream` is complete. */
+int lq2d_apply_delta_device(lq2d_problem *h, const void *d_in, void *d_out, void *stream);
+
+/* q = D_S r: S outer x L inner NBJM sweeps from zero starts (Algorithm 2;
+ * Theorem posdef_preconditioner), device buffers [T+1][K*N][n]. */
+int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const void *d_r,
+                              void *d_q, void *stream);
+
+int lq2d_set_option(lq2d_problem *h, int option, double value);
+int lq2d_get_stats(const lq2d_problem *h, lq2d_stats *out);
+
+/* 0 = FP64 everywhere (default). */
+int lq2d_set_precision(lq2d_problem *h, int mode);
+
+/* Frees every device buffer of the handle; NULL is a no-op. */
+void lq2d_destroy(lq2d_problem *h);
+
+/* Message of the last non-OK status on this thread. */
+const char *lq2d_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQ2D_H */

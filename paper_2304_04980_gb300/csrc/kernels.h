@@ -1,0 +1,73 @@
+// Host-visible launch interface of the per-state-dimension hot kernels.
+// Each state dimension n = 1..kMaxN is compiled in its own translation unit
+// (inst_n*.cu) and exposes one KernelTable.
+#pragma once
+
+#include "common.cuh"
+
+namespace lq2d {
+
+constexpr int kOpThreads = 256;     // threads per block of the node-time kernels
+constexpr int kSweepThreads = 128;  // threads per block of the sweep kernels
+
+// Arguments of one NBJM sweep: theta_out = Phi~^-1 tau with
+//   tau = src                           (first sweep of the first outer step)
+//   tau = r + Xi~ delta_s               (first sweep of a later outer step; tau is kept in rtheta_out)
+//   tau = src + Omega~ theta_in         (later sweeps)
+// and, in the first sweep of a PCG step, the update of Algorithm 1 lines
+// 9-10 fused in front (delta += vartheta d, r -= vartheta y; tau = r).
+struct SweepArgs {
+  const double* src;
+  double* rtheta_out;
+  const double* delta_s;
+  const double* theta_in;
+  double* theta_out;
+  double* r;
+  double* delta;
+  const double* y;
+  const double* d;
+  double* partials;
+};
+
+enum SweepVariant {
+  kSweepPlain = 0,      // tau = src
+  kSweepUpdate = 1,     // PCG update fused, tau = updated r, norms reduced, stop test
+  kSweepOmega = 2,      // tau = src + Omega~ theta_in
+  kSweepOmegaMu = 3,    // as kSweepOmega, plus mu = theta_out' r reduced (last sweep)
+  kSweepXi = 4,         // tau = r + Xi~ delta_s, written to rtheta_out
+};
+
+struct KernelTable {
+  // z = Q~^-1 A~' dn with dn = q + beta d_old (beta from the state when use_beta)
+  void (*delta_z)(const Grid& g, const NodeData& nd, const double* q, const double* dold, double* z,
+                  const SolverState* st, int use_beta, cudaStream_t s);
+  // y = A~ z + B~ R~^-1 B~' dn; in loop mode also writes dn into dout, reduces
+  // y' dn and sets vartheta = mu / (y' dn) (Algorithm 1 lines 7-8)
+  void (*delta_y)(const Grid& g, const NodeData& nd, const double* z, const double* q, const double* dold,
+                  double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s);
+  void (*sweep)(int variant, const Grid& g, const NodeData& nd, const SweepArgs& a, SolverState* st,
+                cudaStream_t s);
+  // KKT residual pieces and cost of (x, u, delta): out[0] = sum of squared
+  // residual entries, out[1] = x'Q~x + u'R~u, out[2] = max |A~x + B~u + omega~|
+  void (*kkt)(const Grid& g, const NodeData& nd, const double* x, const double* u, const double* delta,
+              const double* rhs, double* partials, SolverState* st, double* out, cudaStream_t s);
+};
+
+const KernelTable* kernel_table(int n);
+
+// dimension-generic helpers (kernels_misc.cu)
+void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
+                       int keep_iter, cudaStream_t s);
+void launch_init_residual(const Grid& g, const double* rhs, const double* y, double* r, double* delta,
+                          const double* delta0, double* partials, SolverState* st, cudaStream_t s);
+void launch_norms(const Grid& g, const double* v, int comps, double* partials, unsigned int* counter,
+                  double* out2, cudaStream_t s);
+void launch_build_rhs(const Grid& g, const double* x0, const double* w_api, double* rhs, cudaStream_t s);
+void launch_to_internal(const double* api, double* intl, int NN, int slices, int comps, long long stride,
+                        cudaStream_t s);
+void launch_to_api(const double* intl, double* api, int NN, int slices, int comps, long long stride,
+                   cudaStream_t s);
+void launch_recover_u(const Grid& g, const NodeData& nd, const double* delta, double* u, cudaStream_t s);
+void launch_loop_ctrl(SolverState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+
+}  // namespace lq2d

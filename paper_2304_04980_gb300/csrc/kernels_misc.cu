@@ -1,0 +1,205 @@
+// Dimension-generic kernels: solver-state initialisation, the initial
+// residual, norms, the right-hand side, layout conversion, input recovery and
+// the device-loop control of Algorithm 1.
+#include "kernels.h"
+
+namespace lq2d {
+
+const KernelTable* kernel_table_n1();
+const KernelTable* kernel_table_n2();
+const KernelTable* kernel_table_n3();
+const KernelTable* kernel_table_n4();
+const KernelTable* kernel_table_n5();
+const KernelTable* kernel_table_n6();
+const KernelTable* kernel_table_n7();
+const KernelTable* kernel_table_n8();
+
+const KernelTable* kernel_table(int n) {
+  switch (n) {
+    case 1: return kernel_table_n1();
+    case 2: return kernel_table_n2();
+    case 3: return kernel_table_n3();
+    case 4: return kernel_table_n4();
+    case 5: return kernel_table_n5();
+    case 6: return kernel_table_n6();
+    case 7: return kernel_table_n7();
+    case 8: return kernel_table_n8();
+    default: return nullptr;
+  }
+}
+
+namespace {
+
+__global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
+                                  int keep_iter) {
+  st->mu = 0.0;
+  st->beta = 0.0;
+  st->ydot = 0.0;
+  st->theta = 0.0;
+  st->bnorm2 = *bnorm2;
+  st->stop_mode = stop_mode;
+  st->stop_bound = stop_mode == 0 ? tol * tol * st->bnorm2 : tol;
+  if (!keep_iter) st->iter = 0;
+  st->max_iter = max_iter;
+  st->done = 0;
+  st->have_mu = 0;
+  st->body_count = 0;
+  st->body_cap = max_iter + 2;
+  for (int c = 0; c < 8; ++c) st->counters[c] = 0u;
+}
+
+// r^(0) = r_delta - Delta delta^(0) (Algorithm 1 line 2) with y = Delta delta^(0)
+// given (or zero), delta = delta^(0); then the initial stop test (reading:
+// no iterations when r^(0) already passes).
+__global__ void init_residual_kernel(Grid g, const double* __restrict__ rhs, const double* __restrict__ y,
+                                     double* __restrict__ r, double* __restrict__ delta,
+                                     const double* __restrict__ delta0, double* partials, SolverState* st) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double s2 = 0.0, mx = 0.0;
+  if (idx < g.P) {
+    for (int k = 0; k < g.n; ++k) {
+      const long long e = k * g.Ps + idx;
+      double rv = rhs[e];
+      if (y != nullptr) rv -= y[e];
+      r[e] = rv;
+      if (delta0 != delta) delta[e] = delta0 != nullptr ? delta0[e] : 0.0;
+      s2 += rv * rv;
+      mx = fmax(mx, fabs(rv));
+    }
+  }
+  double t0, t1;
+  if (grid_reduce2<true>(s2, mx, partials, &st->counters[kCntInit], &t0, &t1)) {
+    st->rnorm2 = t0;
+    st->rnorm_inf = t1;
+    const bool pass = st->stop_mode == 0 ? (t0 <= st->stop_bound) : (t1 < st->stop_bound);
+    if (!isfinite(t0)) st->done = kBreakdown;
+    else if (pass) st->done = kConverged;
+    else if (st->iter >= st->max_iter) st->done = kMaxIter;
+  }
+}
+
+__global__ void norms_kernel(Grid g, const double* __restrict__ v, int comps, double* partials, unsigned* counter,
+                             double* out2) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double s2 = 0.0, mx = 0.0;
+  if (idx < g.P)
+    for (int k = 0; k < comps; ++k) {
+      const double x = v[k * g.Ps + idx];
+      s2 += x * x;
+      mx = fmax(mx, fabs(x));
+    }
+  double t0, t1;
+  if (grid_reduce2<true>(s2, mx, partials, counter, &t0, &t1)) {
+    out2[0] = t0;
+    out2[1] = t1;
+  }
+}
+
+// r_delta = -omega~ with omega~ = col(gamma, omega_0, ..., omega_{T-1})
+// (Section II-A, reading A1 for the first block).
+__global__ void build_rhs_kernel(Grid g, const double* __restrict__ x0, const double* __restrict__ w_api,
+                                 double* __restrict__ rhs) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.P) return;
+  const int Tp = g.T + 1;
+  const int p = (int)(idx / Tp), t = (int)(idx % Tp);
+  for (int k = 0; k < g.n; ++k) {
+    double val;
+    if (t == 0) val = -x0[(size_t)p * g.n + k];
+    else val = w_api != nullptr ? -w_api[((size_t)(t - 1) * g.NN + p) * g.n + k] : 0.0;
+    rhs[k * g.Ps + idx] = val;
+  }
+}
+
+// host layout [slice][node][comp]  <->  internal layout [comp][node][slice]
+__global__ void to_internal_kernel(const double* __restrict__ api, double* __restrict__ intl, int NN, int slices,
+                                   int comps, long long stride) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)NN * slices;
+  if (idx >= per * comps) return;
+  const int k = (int)(idx / per);
+  const long long rem = idx % per;
+  const int p = (int)(rem / slices), t = (int)(rem % slices);
+  intl[k * stride + rem] = api[((long long)t * NN + p) * comps + k];
+}
+
+__global__ void to_api_kernel(const double* __restrict__ intl, double* __restrict__ api, int NN, int slices,
+                              int comps, long long stride) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)NN * slices;
+  if (idx >= per * comps) return;
+  const int k = (int)(idx % comps);
+  const long long tp = idx / comps;
+  const int p = (int)(tp % NN), t = (int)(tp / NN);
+  api[idx] = intl[k * stride + (long long)p * slices + t];
+}
+
+// u = R~^-1 B~' delta: u_{p,t} = R_p^-1 B_p' delta_{p,t+1} (Section II-B).
+__global__ void recover_u_kernel(Grid g, NodeData nd, const double* __restrict__ delta, double* __restrict__ u) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)g.NN * g.T) return;
+  const int p = (int)(idx / g.T), t = (int)(idx % g.T);
+  const int n = g.n, m = g.m;
+  const double* RB = nd.RiBt + (size_t)p * m * n;
+  const long long base = (long long)p * (g.T + 1) + t + 1;
+  for (int mm = 0; mm < m; ++mm) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += RB[mm * n + k] * delta[k * g.Ps + base];
+    u[mm * g.Pus + idx] = s;
+  }
+}
+
+// Device-side loop control of Algorithm 1: keep iterating while no stop
+// condition is set and the body has run fewer than body_cap times.
+__global__ void loop_ctrl_kernel(SolverState* st, cudaGraphConditionalHandle h) {
+  const int c = st->body_count + 1;
+  st->body_count = c;
+  int keep = (st->done == kRunning) && (c < st->body_cap);
+  if (st->done == kRunning && !keep) st->done = kLoopCap;
+  cudaGraphSetConditional(h, keep ? 1u : 0u);
+}
+
+inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
+                       int keep_iter, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, stop_mode, bnorm2, keep_iter);
+}
+
+void launch_init_residual(const Grid& g, const double* rhs, const double* y, double* r, double* delta,
+                          const double* delta0, double* partials, SolverState* st, cudaStream_t s) {
+  init_residual_kernel<<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, rhs, y, r, delta, delta0, partials, st);
+}
+
+void launch_norms(const Grid& g, const double* v, int comps, double* partials, unsigned int* counter,
+                  double* out2, cudaStream_t s) {
+  norms_kernel<<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, v, comps, partials, counter, out2);
+}
+
+void launch_build_rhs(const Grid& g, const double* x0, const double* w_api, double* rhs, cudaStream_t s) {
+  build_rhs_kernel<<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, x0, w_api, rhs);
+}
+
+void launch_to_internal(const double* api, double* intl, int NN, int slices, int comps, long long stride,
+                        cudaStream_t s) {
+  const long long total = (long long)NN * slices * comps;
+  to_internal_kernel<<<blocks_for(total, 256), 256, 0, s>>>(api, intl, NN, slices, comps, stride);
+}
+
+void launch_to_api(const double* intl, double* api, int NN, int slices, int comps, long long stride,
+                   cudaStream_t s) {
+  const long long total = (long long)NN * slices * comps;
+  to_api_kernel<<<blocks_for(total, 256), 256, 0, s>>>(intl, api, NN, slices, comps, stride);
+}
+
+void launch_recover_u(const Grid& g, const NodeData& nd, const double* delta, double* u, cudaStream_t s) {
+  recover_u_kernel<<<blocks_for((long long)g.NN * g.T, 256), 256, 0, s>>>(g, nd, delta, u);
+}
+
+void launch_loop_ctrl(SolverState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  loop_ctrl_kernel<<<1, 1, 0, s>>>(st, h);
+}
+
+}  // namespace lq2d

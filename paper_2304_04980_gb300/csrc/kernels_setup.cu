@@ -1,0 +1,409 @@
+// Setup kernels (run once per problem): per-node inverses, the node blocks of
+// Delta's splittings, and the banded block-Cholesky factors of Phi_bar.
+//
+// Paper: Section II-B (structure of Delta: Psi_t = Q_t^-1 + A Q^-1 A' +
+// B R^-1 B', Xi_t = -A Q^-1), Section IV (splittings Delta = Psi~ - Xi~,
+// Psi~ = Phi~ - Omega~ over column pairs v), Section IV-B (one Cholesky
+// factorisation of each Phi_bar_{v,t}, done once before Algorithm 1).
+// With time-invariant blocks Phi_bar_{v,t} takes only two values for t >= 1:
+// one for 1 <= t <= T-1 (class 0) and one for t = T (class 1, Q_T^-1 on the
+// diagonal).  At t = 0, Psi_0 = Q^-1 is node-diagonal, so no factor is needed.
+#include "setup.h"
+
+namespace lq2d {
+
+namespace {
+
+// Lower Cholesky of the leading d x d block of a (row stride d); returns
+// false on a non-positive or non-finite pivot.
+__device__ bool chol_small(double* a, int d) {
+  for (int j = 0; j < d; ++j) {
+    double s = a[j * d + j];
+    for (int k = 0; k < j; ++k) s -= a[j * d + k] * a[j * d + k];
+    if (!(s > 0.0) || !isfinite(s)) return false;
+    const double ljj = sqrt(s);
+    a[j * d + j] = ljj;
+    for (int i = j + 1; i < d; ++i) {
+      double t = a[i * d + j];
+      for (int k = 0; k < j; ++k) t -= a[i * d + k] * a[j * d + k];
+      a[i * d + j] = t / ljj;
+    }
+  }
+  return true;
+}
+
+// inv = (L L')^-1 from the lower Cholesky factor L (d x d).
+__device__ void spd_inverse_from_chol(const double* L, double* inv, int d) {
+  double Li[kMaxN * kMaxN];
+  for (int c = 0; c < d; ++c) {
+    for (int r = 0; r < d; ++r) {
+      if (r < c) { Li[r * d + c] = 0.0; continue; }
+      double s = (r == c) ? 1.0 : 0.0;
+      for (int k = c; k < r; ++k) s -= L[r * d + k] * Li[k * d + c];
+      Li[r * d + c] = s / L[r * d + r];
+    }
+  }
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) {
+      double s = 0.0;
+      for (int k = (r > c ? r : c); k < d; ++k) s += Li[k * d + r] * Li[k * d + c];
+      inv[r * d + c] = s;
+    }
+}
+
+__device__ bool spd_inverse(const double* a, double* inv, int d) {
+  double L[kMaxN * kMaxN];
+  for (int e = 0; e < d * d; ++e) L[e] = a[e];
+  if (!chol_small(L, d)) return false;
+  spd_inverse_from_chol(L, inv, d);
+  return true;
+}
+
+// A_hat block in row p, column r (r = neighbour of p in direction dir).
+__device__ inline const double* ahat_row_block(const double* Aself, const double* Anb, int p, int dir, int n) {
+  return dir == kSelf ? Aself + (size_t)p * n * n : Anb + ((size_t)p * 4 + (dir - 1)) * n * n;
+}
+
+// A_hat block in row r, column p, for r = neighbour of p in direction dir:
+// the west neighbour reaches p through its F (east) block, the east one
+// through E, the north one through H, the south one through G.
+__device__ inline const double* ahat_col_block(const double* Aself, const double* Anb, int r, int dir, int n) {
+  int slot;
+  switch (dir) {
+    case kSelf: return Aself + (size_t)r * n * n;
+    case kWest: slot = 1; break;   // F_r
+    case kEast: slot = 0; break;   // E_r
+    case kNorth: slot = 3; break;  // H_r
+    default: slot = 2; break;      // G_r
+  }
+  return Anb + ((size_t)r * 4 + slot) * n * n;
+}
+
+}  // namespace
+
+// The 13 node offsets (di, dj) with |di| + |dj| <= 2.
+__host__ __device__ int off13_index(int di, int dj) {
+  const int ad = (di < 0 ? -di : di) + (dj < 0 ? -dj : dj);
+  if (ad > 2) return -1;
+  // order: (0,0) (0,-1) (0,1) (-1,0) (1,0) (-1,-1) (-1,1) (1,-1) (1,1) (0,-2) (0,2) (-2,0) (2,0)
+  if (di == 0 && dj == 0) return 0;
+  if (di == 0 && dj == -1) return 1;
+  if (di == 0 && dj == 1) return 2;
+  if (di == -1 && dj == 0) return 3;
+  if (di == 1 && dj == 0) return 4;
+  if (di == -1 && dj == -1) return 5;
+  if (di == -1 && dj == 1) return 6;
+  if (di == 1 && dj == -1) return 7;
+  if (di == 1 && dj == 1) return 8;
+  if (di == 0 && dj == -2) return 9;
+  if (di == 0 && dj == 2) return 10;
+  if (di == -2 && dj == 0) return 11;
+  return 12;  // (2, 0)
+}
+
+__device__ static const int kOff13Di[13] = {0, 0, 0, -1, 1, -1, -1, 1, 1, 0, 0, -2, 2};
+__device__ static const int kOff13Dj[13] = {0, -1, 1, 0, 0, -1, 1, -1, 1, -2, 2, 0, 0};
+
+// Per node: zero the coupling blocks that point off the grid, invert Q, Q_T
+// and R, and form S = B R^-1 B' and R^-1 B'.  Also checks every input entry
+// of the node for finiteness.
+__global__ void setup_nodes_kernel(SetupBuffers sb, int K, int N, int n, int m, int* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= K * N) return;
+  const int i = p / N, j = p % N;
+  const int nn = n * n;
+  int bad = 0;
+  // finiteness of the node's inputs
+  for (int e = 0; e < nn; ++e) {
+    bad |= !isfinite(sb.Aself[(size_t)p * nn + e]);
+    bad |= !isfinite(sb.Qm[(size_t)p * nn + e]);
+    bad |= !isfinite(sb.QTm[(size_t)p * nn + e]);
+  }
+  for (int e = 0; e < 4 * nn; ++e) bad |= !isfinite(sb.Anb[(size_t)p * 4 * nn + e]);
+  for (int e = 0; e < n * m; ++e) bad |= !isfinite(sb.Bm[(size_t)p * n * m + e]);
+  for (int e = 0; e < m * m; ++e) bad |= !isfinite(sb.Rm[(size_t)p * m * m + e]);
+  for (int e = 0; e < n; ++e) bad |= !isfinite(sb.x0[(size_t)p * n + e]);
+  if (bad) atomicOr(status, kSetupNonFinite);
+  // coupling blocks towards boundary states are not part of the unknowns
+  const bool edge[4] = {j == 0, j == N - 1, i == 0, i == K - 1};
+  for (int s = 0; s < 4; ++s)
+    if (edge[s])
+      for (int e = 0; e < nn; ++e) sb.Anb[((size_t)p * 4 + s) * nn + e] = 0.0;
+  double a[kMaxN * kMaxN];
+  // symmetrised copies: the cost weights are symmetric by assumption
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c)
+      a[r * n + c] = 0.5 * (sb.Qm[(size_t)p * nn + r * n + c] + sb.Qm[(size_t)p * nn + c * n + r]);
+  if (!spd_inverse(a, sb.Qi + (size_t)p * nn, n)) atomicOr(status, kSetupNotPD);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c)
+      a[r * n + c] = 0.5 * (sb.QTm[(size_t)p * nn + r * n + c] + sb.QTm[(size_t)p * nn + c * n + r]);
+  if (!spd_inverse(a, sb.QTi + (size_t)p * nn, n)) atomicOr(status, kSetupNotPD);
+  double Ri[kMaxM * kMaxM];
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c)
+      a[r * m + c] = 0.5 * (sb.Rm[(size_t)p * m * m + r * m + c] + sb.Rm[(size_t)p * m * m + c * m + r]);
+  if (!spd_inverse(a, Ri, m)) atomicOr(status, kSetupNotPD);
+  const double* B = sb.Bm + (size_t)p * n * m;
+  // R^-1 B'  (m x n)
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < n; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += Ri[r * m + k] * B[c * m + k];
+      sb.RiBt[(size_t)p * m * n + r * n + c] = s;
+    }
+  // B R^-1 B'  (n x n)
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += B[r * m + k] * sb.RiBt[(size_t)p * m * n + k * n + c];
+      sb.Sb[(size_t)p * nn + r * n + c] = s;
+    }
+}
+
+// Per (node, direction): AQ = A_hat_{p,r} Q_r^-1 and QAt = Q_p^-1 A_hat_{r,p}'.
+// These are the node blocks of Xi~ (Section IV: Xi~ = Psi~ - Delta, whose
+// blocks next to the diagonal are A Q^-1 and Q^-1 A').
+__global__ void setup_aq_kernel(SetupBuffers sb, int K, int N, int n) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= K * N * 5) return;
+  const int p = id / 5, dir = id % 5;
+  const int i = p / N, j = p % N;
+  const int nn = n * n;
+  double* aq = sb.AQ + ((size_t)p * 5 + dir) * nn;
+  double* qat = sb.QAt + ((size_t)p * 5 + dir) * nn;
+  const int r = nbr_node(i, j, dir, K, N);
+  if (r < 0) {
+    for (int e = 0; e < nn; ++e) { aq[e] = 0.0; qat[e] = 0.0; }
+    return;
+  }
+  const double* Apr = ahat_row_block(sb.Aself, sb.Anb, p, dir, n);
+  const double* Arp = ahat_col_block(sb.Aself, sb.Anb, r, dir, n);
+  const double* Qr = sb.Qi + (size_t)r * nn;
+  const double* Qp = sb.Qi + (size_t)p * nn;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double s = 0.0, t = 0.0;
+      for (int c = 0; c < n; ++c) {
+        s += Apr[a * n + c] * Qr[c * n + b];
+        t += Qp[a * n + c] * Arp[b * n + c];
+      }
+      aq[a * n + b] = s;
+      qat[a * n + b] = t;
+    }
+}
+
+// Per (node p, offset o of the 13-point stencil): M_{p,q} =
+// sum_r A_hat_{p,r} Q_r^-1 A_hat_{q,r}' over the common neighbours r of p and
+// q: the spatial blocks of A_hat Q^-1 A_hat' in Psi_t (Section II-B).
+__global__ void setup_m13_kernel(SetupBuffers sb, int K, int N, int n) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= K * N * 13) return;
+  const int p = id / 13, o = id % 13;
+  const int i = p / N, j = p % N;
+  const int nn = n * n;
+  double* M = sb.M13 + ((size_t)p * 13 + o) * nn;
+  for (int e = 0; e < nn; ++e) M[e] = 0.0;
+  const int qi = i + kOff13Di[o], qj = j + kOff13Dj[o];
+  if (qi < 0 || qi >= K || qj < 0 || qj >= N) return;
+  const int q = qi * N + qj;
+  for (int dp = 0; dp < 5; ++dp) {
+    const int r = nbr_node(i, j, dp, K, N);
+    if (r < 0) continue;
+    const int ri = r / N, rj = r % N;
+    const int di = ri - qi, dj = rj - qj;
+    int dq;
+    if (di == 0 && dj == 0) dq = kSelf;
+    else if (di == 0 && dj == -1) dq = kWest;
+    else if (di == 0 && dj == 1) dq = kEast;
+    else if (di == -1 && dj == 0) dq = kNorth;
+    else if (di == 1 && dj == 0) dq = kSouth;
+    else continue;
+    const double* aq = sb.AQ + ((size_t)p * 5 + dp) * nn;           // A_hat_{p,r} Q_r^-1
+    const double* Aqr = ahat_row_block(sb.Aself, sb.Anb, q, dq, n);  // A_hat_{q,r}
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < n; ++c) s += aq[a * n + c] * Aqr[b * n + c];
+        M[a * n + b] += s;
+      }
+  }
+}
+
+// Omega~ blocks: Omega~ = Phi~ - Psi~ holds minus the couplings of Psi~
+// between a node and the five nodes of the neighbouring column pairs.
+__global__ void setup_omega_kernel(SetupBuffers sb, int K, int N, int n) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= K * N * 5) return;
+  const int p = id / 5, o = id % 5;
+  const int i = p / N, j = p % N;
+  const int nn = n * n;
+  double* Om = sb.Om + ((size_t)p * 5 + o) * nn;
+  const int q = offpair_node(i, j, o, K, N);
+  if (q < 0) {
+    for (int e = 0; e < nn; ++e) Om[e] = 0.0;
+    return;
+  }
+  const int idx = off13_index(q / N - i, q % N - j);
+  const double* M = sb.M13 + ((size_t)p * 13 + idx) * nn;
+  for (int e = 0; e < nn; ++e) Om[e] = -M[e];
+}
+
+// Banded block-Cholesky factorisation of Phi_bar_{v,class} (Section IV-B),
+// one warp per (column pair v, class).  Unknowns are ordered by pair-row i
+// (the two nodes (i, 2v) and (i, 2v+1)) and, inside a pair-row, by node then
+// component, so Phi_bar is block-pentadiagonal in 2n x 2n pair-row blocks and
+// its Cholesky factor keeps that band:
+//   L2_i = A_{i,i-2} L0_{i-2}^-T
+//   L1_i = (A_{i,i-1} - L2_i L1_{i-1}') L0_{i-1}^-T
+//   L0_i L0_i' = A_{i,i} - L1_i L1_i' - L2_i L2_i'
+// The diagonal factors are stored inverted.  A missing second column (odd N)
+// is carried as a decoupled identity block, whose solution is zero.
+// Record of pair-row i (G2 = 2n, blocks G2 x G2 row-major):
+//   [L2'][L1'][L0^-1'] (read by the forward substitution)
+//   [L2 ][L1 ][L0^-1 ] (read by the backward substitution)
+__global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V, long long fac_rec,
+                                    long long fac_vc, int* status) {
+  extern __shared__ double smem[];
+  const int vc = blockIdx.x;
+  const int v = vc >> 1, cls = vc & 1;
+  const int lane = threadIdx.x;
+  const int G2 = 2 * n, BS = G2 * G2;
+  double* Aii = smem;
+  double* Aim1 = Aii + BS;
+  double* Aim2 = Aim1 + BS;
+  double* L2 = Aim2 + BS;
+  double* L1 = L2 + BS;
+  double* C = L1 + BS;
+  double* tmp = C + BS;
+  double* prevL0 = tmp + BS;       // [2][BS]: L0^-1 of pair-rows i-1, i-2
+  double* prevL1 = prevL0 + 2 * BS;  // L1 of pair-row i-1
+  __shared__ int bad;
+  if (lane == 0) bad = 0;
+  const int nn = n * n;
+  const double* Qd = cls == 0 ? sb.Qi : sb.QTi;
+  const bool two_cols = (2 * v + 1) < N;
+  int cur = 0;  // index of the L0^-1 of pair-row i-1 inside prevL0
+  __syncwarp();
+  for (int i = 0; i < K; ++i) {
+    // --- assemble the three blocks of row i of Phi_bar
+    for (int e = lane; e < 3 * BS; e += 32) {
+      const int blk = e / BS, rc = e % BS;
+      const int a = rc / G2, b = rc % G2;
+      const int ja = a / n, ka = a % n, jb = b / n, kb = b % n;
+      const int di = -blk;  // column node lives in pair-row i - blk
+      double val = 0.0;
+      const bool colA = (ja == 0) || two_cols;
+      const bool colB = (jb == 0) || two_cols;
+      if (i + di >= 0) {
+        if (colA && colB) {
+          const int p = i * N + 2 * v + ja;
+          const int o = off13_index(di, jb - ja);
+          if (o >= 0) val = sb.M13[((size_t)p * 13 + o) * nn + ka * n + kb];
+          if (blk == 0 && ja == jb) val += Qd[(size_t)p * nn + ka * n + kb] + sb.Sb[(size_t)p * nn + ka * n + kb];
+        } else if (blk == 0 && ja == jb) {
+          val = (ka == kb) ? 1.0 : 0.0;  // decoupled stand-in for the missing column
+        }
+      }
+      (blk == 0 ? Aii : blk == 1 ? Aim1 : Aim2)[rc] = val;
+    }
+    __syncwarp();
+    const double* L0m1 = prevL0 + cur * BS;        // pair-row i-1
+    const double* L0m2 = prevL0 + (cur ^ 1) * BS;  // pair-row i-2
+    // --- L2 = A_{i,i-2} L0_{i-2}^-T
+    for (int e = lane; e < BS; e += 32) {
+      const int a = e / G2, b = e % G2;
+      double s = 0.0;
+      if (i >= 2)
+        for (int c = 0; c < G2; ++c) s += Aim2[a * G2 + c] * L0m2[b * G2 + c];
+      L2[e] = s;
+    }
+    __syncwarp();
+    // --- tmp = A_{i,i-1} - L2 L1_{i-1}'
+    for (int e = lane; e < BS; e += 32) {
+      const int a = e / G2, b = e % G2;
+      double s = Aim1[e];
+      if (i >= 2)
+        for (int c = 0; c < G2; ++c) s -= L2[a * G2 + c] * prevL1[b * G2 + c];
+      tmp[e] = s;
+    }
+    __syncwarp();
+    // --- L1 = tmp L0_{i-1}^-T
+    for (int e = lane; e < BS; e += 32) {
+      const int a = e / G2, b = e % G2;
+      double s = 0.0;
+      if (i >= 1)
+        for (int c = 0; c < G2; ++c) s += tmp[a * G2 + c] * L0m1[b * G2 + c];
+      L1[e] = s;
+    }
+    __syncwarp();
+    // --- C = A_{i,i} - L1 L1' - L2 L2'
+    for (int e = lane; e < BS; e += 32) {
+      const int a = e / G2, b = e % G2;
+      double s = Aii[e];
+      for (int c = 0; c < G2; ++c) s -= L1[a * G2 + c] * L1[b * G2 + c] + L2[a * G2 + c] * L2[b * G2 + c];
+      C[e] = s;
+    }
+    __syncwarp();
+    // --- C = L0 L0' (right-looking, in place, lower triangle)
+    for (int jc = 0; jc < G2; ++jc) {
+      if (lane == 0) {
+        const double d = C[jc * G2 + jc];
+        if (!(d > 0.0) || !isfinite(d)) bad = 1;
+        C[jc * G2 + jc] = sqrt(d > 0.0 ? d : 1.0);
+      }
+      __syncwarp();
+      const double piv = C[jc * G2 + jc];
+      for (int r = jc + 1 + lane; r < G2; r += 32) C[r * G2 + jc] /= piv;
+      __syncwarp();
+      for (int e = lane; e < BS; e += 32) {
+        const int r = e / G2, c = e % G2;
+        if (c > jc && r >= c) C[e] -= C[r * G2 + jc] * C[c * G2 + jc];
+      }
+      __syncwarp();
+    }
+    // --- L0^-1 into the slot of pair-row i-2 (no longer needed); lane c
+    //     solves column c of L0 X = I by forward substitution
+    double* L0i = prevL0 + (cur ^ 1) * BS;
+    if (lane < G2) {
+      const int c = lane;
+      for (int r = 0; r < G2; ++r) {
+        if (r < c) { L0i[r * G2 + c] = 0.0; continue; }
+        double s = (r == c) ? 1.0 : 0.0;
+        for (int k = c; k < r; ++k) s -= C[r * G2 + k] * L0i[k * G2 + c];
+        L0i[r * G2 + c] = s / C[r * G2 + r];
+      }
+    }
+    __syncwarp();
+    // --- store the record
+    double* rec = sb.fac + (size_t)vc * fac_vc + (size_t)i * fac_rec;
+    for (int e = lane; e < BS; e += 32) {
+      const int a = e / G2, b = e % G2;
+      const int et = b * G2 + a;  // transposed position
+      rec[0 * BS + et] = L2[e];
+      rec[1 * BS + et] = L1[e];
+      rec[2 * BS + et] = L0i[e];
+      rec[3 * BS + e] = L2[e];
+      rec[4 * BS + e] = L1[e];
+      rec[5 * BS + e] = L0i[e];
+      prevL1[e] = L1[e];
+    }
+    __syncwarp();
+    cur ^= 1;  // the slot just written becomes "pair-row i-1"
+  }
+  if (lane == 0 && bad) atomicOr(status, kSetupPhiNotPD);
+  (void)V;
+}
+
+void launch_setup(const SetupBuffers& sb, int K, int N, int n, int m, int V, long long fac_rec,
+                  long long fac_vc, int* d_status, cudaStream_t s) {
+  const int NN = K * N;
+  setup_nodes_kernel<<<(NN + 127) / 128, 128, 0, s>>>(sb, K, N, n, m, d_status);
+  setup_aq_kernel<<<(NN * 5 + 127) / 128, 128, 0, s>>>(sb, K, N, n);
+  setup_m13_kernel<<<(NN * 13 + 127) / 128, 128, 0, s>>>(sb, K, N, n);
+  setup_omega_kernel<<<(NN * 5 + 127) / 128, 128, 0, s>>>(sb, K, N, n);
+  const size_t shm = (size_t)11 * (2 * n) * (2 * n) * sizeof(double);
+  setup_factor_kernel<<<V * 2, 32, shm, s>>>(sb, K, N, n, V, fac_rec, fac_vc, d_status);
+}
+
+}  // namespace lq2d

@@ -1,0 +1,688 @@
+// C-ABI library: problem handle, setup, and the PCG driver (Algorithm 1 with
+// Algorithm 2 as preconditioner) over the CUDA kernels of this directory.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lq2d.h"
+#include "kernels.h"
+#include "setup.h"
+
+using namespace lq2d;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define LQ_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? LQ2D_ENOMEM : LQ2D_ECUDA,                  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+struct GraphEntry {
+  int S = 0, L = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+constexpr int kMaxGraphs = 8;
+constexpr int kStreamChunk = 4;  // steps enqueued between stop-flag reads (driver 1)
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct lq2d_problem {
+  Grid g{};
+  NodeData nd{};
+  SetupBuffers sb{};
+  const KernelTable* kt = nullptr;
+  cudaStream_t priv = nullptr;  // private stream for graph capture
+  std::vector<void*> allocs;
+  // vectors, internal layout
+  double *rhs = nullptr, *delta = nullptr, *r = nullptr, *d = nullptr, *y = nullptr, *z = nullptr;
+  double *thA = nullptr, *thB = nullptr, *rth = nullptr, *u = nullptr;
+  double *w_aff = nullptr;     // active affine terms, host layout [T][NN][n] (NULL: none)
+  double *w_buf = nullptr;     // their device buffer, allocated on first use
+  double* stage_x = nullptr;   // host-layout staging, [T+1][NN][n]
+  double* stage_u = nullptr;   // [T][NN][m]
+  double* partials = nullptr;
+  double* bnorm = nullptr;     // [2]: ||r_delta||_2^2, ||r_delta||_inf
+  double* kkt_out = nullptr;   // [4]
+  int* setup_status = nullptr;
+  SolverState* st = nullptr;
+  // pinned host mirrors
+  SolverState* h_st = nullptr;
+  double* h_kkt = nullptr;
+  int* h_done = nullptr;  // [2] stop-flag slots for driver 1
+  // options
+  int stop_mode = 0;
+  int driver = 0;
+  int timing = 0;
+  int max_restarts = 3;
+  GraphEntry graphs[kMaxGraphs];
+  int ngraphs = 0;
+  lq2d_stats stats{};
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace {
+
+int dev_alloc(lq2d_problem* h, double** p, size_t count) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(double) + 256);
+  if (e != cudaSuccess) return fail(LQ2D_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(ptr);
+  *p = static_cast<double*>(ptr);
+  return LQ2D_OK;
+}
+
+void free_all(lq2d_problem* h) {
+  for (int i = 0; i < h->ngraphs; ++i) {
+    if (h->graphs[i].exec) cudaGraphExecDestroy(h->graphs[i].exec);
+    if (h->graphs[i].graph) cudaGraphDestroy(h->graphs[i].graph);
+  }
+  h->ngraphs = 0;
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->h_kkt) cudaFreeHost(h->h_kkt);
+  if (h->h_done) cudaFreeHost(h->h_done);
+  if (h->priv) cudaStreamDestroy(h->priv);
+  h->h_st = nullptr;
+  h->h_kkt = nullptr;
+  h->h_done = nullptr;
+  h->priv = nullptr;
+}
+
+int check_dims(int K, int N, int T, int n, int m) {
+  if (K < 1 || N < 1 || T < 1) return fail(LQ2D_EINVAL, "K, N and T must be >= 1");
+  if (n < 1 || n > kMaxN) return fail(LQ2D_EINVAL, "n must be in 1..8");
+  if (m < 1 || m > kMaxM) return fail(LQ2D_EINVAL, "m must be in 1..8");
+  const long long NN = (long long)K * N;
+  if (NN * (T + 1) * (long long)n > (1LL << 40) || NN > (1LL << 30))
+    return fail(LQ2D_EINVAL, "problem too large");
+  return LQ2D_OK;
+}
+
+int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
+  Grid& g = h->g;
+  g.K = K; g.N = N; g.T = T; g.n = n; g.m = m;
+  g.V = (N + 1) / 2;
+  g.NN = K * N;
+  g.P = (long long)g.NN * (T + 1);
+  g.Ps = round_up(g.P, 64);
+  g.Pu = (long long)g.NN * T;
+  g.Pus = round_up(g.Pu, 64);
+  h->kt = kernel_table(n);
+  if (!h->kt) return fail(LQ2D_EINVAL, "no kernels for this n");
+  LQ_CUDA(cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking));
+  const size_t NN = g.NN, nn = (size_t)n * n;
+  int rc;
+#define ALLOC(ptr, cnt) \
+  if ((rc = dev_alloc(h, &(ptr), (cnt))) != LQ2D_OK) return rc
+  SetupBuffers& sb = h->sb;
+  ALLOC(sb.Aself, NN * nn);
+  ALLOC(sb.Anb, NN * 4 * nn);
+  ALLOC(sb.Bm, NN * n * m);
+  ALLOC(sb.Qm, NN * nn);
+  ALLOC(sb.QTm, NN * nn);
+  ALLOC(sb.Rm, NN * m * m);
+  ALLOC(sb.x0, NN * n);
+  ALLOC(sb.Qi, NN * nn);
+  ALLOC(sb.QTi, NN * nn);
+  ALLOC(sb.Sb, NN * nn);
+  ALLOC(sb.RiBt, NN * m * n);
+  ALLOC(sb.AQ, NN * 5 * nn);
+  ALLOC(sb.QAt, NN * 5 * nn);
+  ALLOC(sb.M13, NN * 13 * nn);
+  ALLOC(sb.Om, NN * 5 * nn);
+  const long long fac_rec = 24LL * n * n;
+  const long long fac_vc = fac_rec * K;
+  ALLOC(sb.fac, (size_t)g.V * 2 * fac_vc);
+  const size_t vec = (size_t)g.Ps * n;
+  ALLOC(h->rhs, vec);
+  ALLOC(h->delta, vec);
+  ALLOC(h->r, vec);
+  ALLOC(h->d, vec);
+  ALLOC(h->y, vec);
+  ALLOC(h->z, vec);
+  ALLOC(h->thA, vec);
+  ALLOC(h->thB, vec);
+  ALLOC(h->rth, vec);
+  ALLOC(h->u, (size_t)g.Pus * m);
+  ALLOC(h->stage_x, (size_t)g.P * n);
+  ALLOC(h->stage_u, (size_t)g.Pu * m);
+  // partials: two values per block, two reductions in the KKT kernel
+  const long long op_blocks = (g.P + kOpThreads - 1) / kOpThreads;
+  const long long sw_blocks = ((long long)g.V * (T + 1) * 32 + kSweepThreads - 1) / kSweepThreads;
+  const long long pblocks = op_blocks > sw_blocks ? op_blocks : sw_blocks;
+  ALLOC(h->partials, (size_t)pblocks * 4 + 64);
+  double* misc = nullptr;
+  ALLOC(misc, 64);
+  h->bnorm = misc;
+  h->kkt_out = misc + 8;
+  h->setup_status = reinterpret_cast<int*>(misc + 16);
+  h->st = reinterpret_cast<SolverState*>(misc + 24);
+  static_assert(sizeof(SolverState) <= 40 * sizeof(double), "state slot");
+#undef ALLOC
+  LQ_CUDA(cudaMemset(misc, 0, 64 * sizeof(double) + 256));
+  LQ_CUDA(cudaMemset(h->d, 0, vec * sizeof(double)));
+  LQ_CUDA(cudaMallocHost(&h->h_st, sizeof(SolverState)));
+  LQ_CUDA(cudaMallocHost(&h->h_kkt, 8 * sizeof(double)));
+  LQ_CUDA(cudaMallocHost(&h->h_done, 2 * sizeof(int)));
+  NodeData& nd = h->nd;
+  nd.Aself = sb.Aself; nd.Anb = sb.Anb; nd.Bm = sb.Bm; nd.Qm = sb.Qm; nd.QTm = sb.QTm; nd.Rm = sb.Rm;
+  nd.Qi = sb.Qi; nd.QTi = sb.QTi; nd.Sb = sb.Sb; nd.RiBt = sb.RiBt; nd.Om = sb.Om; nd.AQ = sb.AQ;
+  nd.QAt = sb.QAt; nd.fac = sb.fac; nd.fac_rec = fac_rec; nd.fac_vc = fac_vc;
+  return LQ2D_OK;
+}
+
+// Setup on `s`: inverses, splitting blocks, factors, right-hand side and its
+// norm; then waits for `s` and checks the setup status.
+int run_setup(lq2d_problem* h, cudaStream_t s) {
+  const Grid& g = h->g;
+  LQ_CUDA(cudaMemsetAsync(h->setup_status, 0, sizeof(int), s));
+  launch_setup(h->sb, g.K, g.N, g.n, g.m, g.V, h->nd.fac_rec, h->nd.fac_vc, h->setup_status, s);
+  launch_build_rhs(g, h->sb.x0, h->w_aff, h->rhs, s);
+  launch_norms(g, h->rhs, g.n, h->partials, &h->st->counters[kCntAux], h->bnorm, s);
+  LQ_CUDA(cudaMemcpyAsync(&h->h_done[0], h->setup_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  const int status = h->h_done[0];
+  if (status & kSetupNonFinite) return fail(LQ2D_EINVAL, "non-finite input entry");
+  if (status & kSetupNotPD) return fail(LQ2D_ENOTPD, "Q, Q_T or R is not positive definite");
+  if (status & kSetupPhiNotPD) return fail(LQ2D_ENOTPD, "a Phi_bar block is not positive definite");
+  return LQ2D_OK;
+}
+
+int copy_inputs(lq2d_problem* h, const double* const src[7], cudaMemcpyKind kind, cudaStream_t s) {
+  const Grid& g = h->g;
+  const size_t NN = g.NN, n = g.n, m = g.m;
+  double* dst[7] = {h->sb.Aself, h->sb.Anb, h->sb.Bm, h->sb.Qm, h->sb.Rm, h->sb.QTm, h->sb.x0};
+  const size_t cnt[7] = {NN * n * n, NN * 4 * n * n, NN * n * m, NN * n * n, NN * m * m, NN * n * n, NN * n};
+  for (int a = 0; a < 7; ++a) {
+    if (!src[a]) return fail(LQ2D_EINVAL, "null input array");
+    LQ_CUDA(cudaMemcpyAsync(dst[a], src[a], cnt[a] * sizeof(double), kind, s));
+  }
+  return LQ2D_OK;
+}
+
+int create_common(lq2d_problem** out, int K, int N, int T, int n, int m, const double* const src[7],
+                  cudaMemcpyKind kind, cudaStream_t s) {
+  if (!out) return fail(LQ2D_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_dims(K, N, T, n, m);
+  if (rc) return rc;
+  lq2d_problem* h = new lq2d_problem();
+  rc = allocate(h, K, N, T, n, m);
+  if (!rc) rc = copy_inputs(h, src, kind, s);
+  if (!rc) rc = run_setup(h, s);
+  if (rc) {
+    std::string keep = g_err;
+    free_all(h);
+    delete h;
+    g_err = keep;
+    return rc;
+  }
+  *out = h;
+  return LQ2D_OK;
+}
+
+// One preconditioner application q = D_S r_in (Algorithm 2, S x L sweeps
+// from zero starts).  fuse_update: the first sweep also performs Algorithm 1
+// lines 9-11; mu: the last sweep reduces mu = q' r.  Returns the buffer
+// holding q (thB, since S*L is even).
+const double* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
+                              const double* r_in, cudaStream_t s, bool timing) {
+  double* bufs[2] = {h->thA, h->thB};
+  int out_i = 0;
+  const double* prev = nullptr;
+  for (int so = 0; so < S; ++so) {
+    for (int l = 0; l < L; ++l) {
+      SweepArgs a{};
+      a.partials = h->partials;
+      a.theta_out = bufs[out_i];
+      int variant;
+      if (l == 0 && so == 0) {
+        variant = fuse_update ? kSweepUpdate : kSweepPlain;
+        a.src = r_in;
+        a.r = const_cast<double*>(r_in);
+        a.delta = h->delta;
+        a.y = h->y;
+        a.d = h->d;
+      } else if (l == 0) {
+        variant = kSweepXi;
+        a.src = r_in;
+        a.delta_s = prev;
+        a.rtheta_out = h->rth;
+      } else {
+        variant = (mu && so == S - 1 && l == L - 1) ? kSweepOmegaMu : kSweepOmega;
+        a.src = so == 0 ? r_in : h->rth;
+        a.theta_in = prev;
+        a.r = const_cast<double*>(r_in);
+      }
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (timing) {
+        const size_t k = h->ev_pool.size();
+        h->ev_pool.resize(k + 2);
+        cudaEventCreate(&h->ev_pool[k]);
+        cudaEventCreate(&h->ev_pool[k + 1]);
+        e0 = h->ev_pool[k];
+        e1 = h->ev_pool[k + 1];
+        cudaEventRecord(e0, s);
+      }
+      h->kt->sweep(variant, h->g, h->nd, a, st, s);
+      if (timing) cudaEventRecord(e1, s);
+      prev = bufs[out_i];
+      out_i ^= 1;
+    }
+  }
+  return prev;
+}
+
+void enqueue_delta(lq2d_problem* h, const double* q, const double* dold, double* dout, double* y,
+                   SolverState* st, bool loop, cudaStream_t s, bool timing) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (timing) {
+    // events of the Delta apply are kept after the sweep events, tagged by parity
+    const size_t k = h->ev_pool.size();
+    h->ev_pool.resize(k + 2);
+    cudaEventCreate(&h->ev_pool[k]);
+    cudaEventCreate(&h->ev_pool[k + 1]);
+    e0 = h->ev_pool[k];
+    e1 = h->ev_pool[k + 1];
+    cudaEventRecord(e0, s);
+  }
+  h->kt->delta_z(h->g, h->nd, q, dold, h->z, st, loop ? 1 : 0, s);
+  h->kt->delta_y(h->g, h->nd, h->z, q, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+  if (timing) cudaEventRecord(e1, s);
+}
+
+// One PCG step (Algorithm 1 lines 7-14): y = Delta d with d = q + beta d
+// fused in, then the preconditioner with the update fused into its first
+// sweep and mu into its last.
+void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
+  enqueue_delta(h, h->thB, h->d, h->d, h->y, h->st, true, s, timing);
+  enqueue_precond(h, S, L, true, true, h->st, h->r, s, timing);
+}
+
+int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
+  for (int i = 0; i < h->ngraphs; ++i)
+    if (h->graphs[i].S == S && h->graphs[i].L == L) {
+      *exec = h->graphs[i].exec;
+      return LQ2D_OK;
+    }
+  if (h->ngraphs == kMaxGraphs) {
+    cudaGraphExecDestroy(h->graphs[0].exec);
+    cudaGraphDestroy(h->graphs[0].graph);
+    for (int i = 1; i < kMaxGraphs; ++i) h->graphs[i - 1] = h->graphs[i];
+    h->ngraphs--;
+  }
+  GraphEntry ge;
+  ge.S = S;
+  ge.L = L;
+  LQ_CUDA(cudaGraphCreate(&ge.graph, 0));
+  cudaGraphConditionalHandle hc;
+  LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, ge.graph, 1u, cudaGraphCondAssignDefault));
+  // zero-initialised storage: the struct's union has no default constructor
+  alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_storage, 0, sizeof(cp_storage));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  LQ_CUDA(cudaGraphAddNode(&node, ge.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  LQ_CUDA(cudaStreamBeginCaptureToGraph(h->priv, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(h, S, L, h->priv, false);
+  launch_loop_ctrl(h->st, hc, h->priv);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(h->priv, &captured);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(ge.graph);
+    return fail(LQ2D_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(ge.graph);
+    return fail(LQ2D_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+  }
+  h->graphs[h->ngraphs++] = ge;
+  *exec = ge.exec;
+  return LQ2D_OK;
+}
+
+int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
+  const bool use_stream = h->driver == 1 || h->timing;
+  if (!use_stream) {
+    cudaGraphExec_t exec;
+    int rc = get_graph(h, S, L, &exec);
+    if (rc) return rc;
+    LQ_CUDA(cudaGraphLaunch(exec, s));
+    return LQ2D_OK;
+  }
+  // driver 1: steps enqueued from the host in chunks; the stop flag of the
+  // previous chunk is read while the current one runs.  Kernels return at
+  // once when the flag is set, so the overshoot costs only empty launches.
+  const int cap = max_iter + 2;
+  int enq = 0;
+  cudaEvent_t flag_ev[2];
+  LQ_CUDA(cudaEventCreateWithFlags(&flag_ev[0], cudaEventDisableTiming));
+  LQ_CUDA(cudaEventCreateWithFlags(&flag_ev[1], cudaEventDisableTiming));
+  int slot = 0;
+  bool pending[2] = {false, false};
+  int rc = LQ2D_OK;
+  while (enq < cap) {
+    for (int c = 0; c < kStreamChunk && enq < cap; ++c, ++enq) enqueue_step(h, S, L, s, h->timing != 0);
+    cudaMemcpyAsync(&h->h_done[slot], &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(flag_ev[slot], s);
+    pending[slot] = true;
+    slot ^= 1;
+    if (pending[slot]) {
+      cudaEventSynchronize(flag_ev[slot]);
+      pending[slot] = false;
+      if (h->h_done[slot] != 0) break;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) rc = fail(LQ2D_ECUDA, std::string("stream loop: ") + cudaGetErrorString(e));
+  cudaEventDestroy(flag_ev[0]);
+  cudaEventDestroy(flag_ev[1]);
+  return rc;
+}
+
+// Sums the event pairs of the timed steps.  Pool order per step: one pair
+// around the Delta apply, then S*L pairs around the sweeps.  Only launches
+// that did work are counted: in the step that met the stop test the sweeps
+// after the first return at once, and later steps are empty.
+void collect_timing(lq2d_problem* h, int S, int L, int steps_done) {
+  const size_t per = 2 + 2 * (size_t)S * L;
+  const size_t steps = h->ev_pool.size() / per;
+  for (size_t k = 0; k < steps && (int)k < steps_done; ++k) {
+    const size_t b = k * per;
+    const bool last = (int)k == steps_done - 1;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[b], h->ev_pool[b + 1]) == cudaSuccess) {
+      h->stats.delta_ms += ms;
+      h->stats.delta_launches += 1;
+    }
+    const size_t nsw = last ? 1 : (size_t)S * L;
+    for (size_t w = 0; w < nsw; ++w) {
+      if (cudaEventElapsedTime(&ms, h->ev_pool[b + 2 + 2 * w], h->ev_pool[b + 3 + 2 * w]) == cudaSuccess) {
+        h->stats.sweep_ms += ms;
+        h->stats.sweep_launches += 1;
+      }
+    }
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+}
+
+// The full solve on device buffers (host layout), ordered on s.
+int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const double* d_delta0, double* d_x,
+               double* d_u, double* d_costate, int* iterations, double* rel_kkt, cudaStream_t s) {
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(LQ2D_EINVAL, "tol must be positive and finite");
+  if (S < 1) return fail(LQ2D_EINVAL, "outer_S must be >= 1");
+  if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2 (Theorem posdef_preconditioner)");
+  if (max_iter < 0) return fail(LQ2D_EINVAL, "max_iter must be >= 0");
+  const Grid& g = h->g;
+  const KernelTable* kt = h->kt;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  h->ev_pool.clear();
+  launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, s);
+  if (d_delta0) {
+    launch_to_internal(d_delta0, h->thA, g.NN, g.T + 1, g.n, g.Ps, s);
+    kt->delta_z(g, h->nd, h->thA, nullptr, h->z, nullptr, 0, s);
+    kt->delta_y(g, h->nd, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
+    launch_init_residual(g, h->rhs, h->y, h->r, h->delta, h->thA, h->partials, h->st, s);
+  } else {
+    launch_init_residual(g, h->rhs, nullptr, h->r, h->delta, nullptr, h->partials, h->st, s);
+  }
+  int restarts = 0;
+  int status = LQ2D_OK;
+  double rel = 0.0;
+  int iter_before = 0;
+  for (;;) {
+    enqueue_precond(h, S, L, false, true, h->st, h->r, s, false);
+    LQ_CUDA(cudaMemsetAsync(h->d, 0, (size_t)g.Ps * g.n * sizeof(double), s));
+    int rc = run_loop(h, S, L, max_iter, s);
+    if (rc) return rc;
+    // recovery (Section II-B): x = Q~^-1 A~' delta into z, u = R~^-1 B~' delta,
+    // and the full KKT residual of (x, u, delta)
+    kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
+    launch_recover_u(g, h->nd, h->delta, h->u, s);
+    kt->kkt(g, h->nd, h->z, h->u, h->delta, h->rhs, h->partials, h->st, h->kkt_out, s);
+    LQ_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    LQ_CUDA(cudaMemcpyAsync(h->h_kkt, h->kkt_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LQ_CUDA(cudaStreamSynchronize(s));
+    LQ_CUDA(cudaGetLastError());
+    const SolverState& hs = *h->h_st;
+    if (h->timing) collect_timing(h, S, L, hs.iter - iter_before);
+    iter_before = hs.iter;
+    const double bn = std::sqrt(hs.bnorm2);
+    rel = bn > 0 ? std::sqrt(h->h_kkt[0]) / bn : std::sqrt(h->h_kkt[0]);
+    const bool true_pass = h->stop_mode == 0 ? (rel <= tol || h->h_kkt[0] == 0.0) : (h->h_kkt[2] < tol);
+    if (hs.done == kConverged && !true_pass && restarts < h->max_restarts && hs.iter < max_iter) {
+      // the recurrence residual passed but the true one did not: restart
+      // from the current iterate with r = r_delta - Delta delta
+      ++restarts;
+      launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 1, s);
+      kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
+      kt->delta_y(g, h->nd, h->z, h->delta, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
+      launch_init_residual(g, h->rhs, h->y, h->r, h->delta, h->delta, h->partials, h->st, s);
+      continue;
+    }
+    switch (hs.done) {
+      case kConverged: status = true_pass ? LQ2D_OK : LQ2D_ENOCONV; break;
+      case kMaxIter: status = LQ2D_ENOCONV; break;
+      case kBreakdown: status = LQ2D_EBREAKDOWN; break;
+      case kLoopCap: status = LQ2D_ETIMEOUT; break;
+      default: status = LQ2D_ECUDA; break;
+    }
+    h->stats.iterations = hs.iter;
+    h->stats.restarts = restarts;
+    h->stats.rel_residual = bn > 0 ? std::sqrt(hs.rnorm2) / bn : std::sqrt(hs.rnorm2);
+    h->stats.rel_kkt_residual = rel;
+    h->stats.kkt_inf = h->h_kkt[2];
+    h->stats.cost = 0.5 * h->h_kkt[1];
+    h->stats.status = status;
+    break;
+  }
+  if (d_x) launch_to_api(h->z, d_x, g.NN, g.T + 1, g.n, g.Ps, s);
+  if (d_u) launch_to_api(h->u, d_u, g.NN, g.T, g.m, g.Pus, s);
+  if (d_costate) launch_to_api(h->delta, d_costate, g.NN, g.T + 1, g.n, g.Ps, s);
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  if (iterations) *iterations = h->stats.iterations;
+  if (rel_kkt) *rel_kkt = rel;
+  if (status == LQ2D_ENOCONV) return fail(status, "max_iter reached before the tolerance");
+  if (status == LQ2D_EBREAKDOWN) return fail(status, "breakdown: y'd <= 0 or a non-finite scalar");
+  if (status == LQ2D_ETIMEOUT) return fail(status, "device loop cap reached");
+  if (status != LQ2D_OK) return fail(status, "solver state not set");
+  return LQ2D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lq2d_create(lq2d_problem** out, int K, int N, int T, int n, int m, const double* A_self, const double* A_nbr,
+                const double* B, const double* Q, const double* R, const double* Q_T, const double* x0) {
+  const double* src[7] = {A_self, A_nbr, B, Q, R, Q_T, x0};
+  int rc = check_dims(K, N, T, n, m);
+  if (rc) return rc;
+  // reject non-finite host input before touching the device
+  const size_t NN = (size_t)K * N;
+  const size_t cnt[7] = {NN * n * n, NN * 4 * n * n, NN * n * m, NN * n * n, NN * m * m, NN * n * n, NN * n};
+  for (int a = 0; a < 7; ++a) {
+    if (!src[a]) return fail(LQ2D_EINVAL, "null input array");
+    for (size_t e = 0; e < cnt[a]; ++e)
+      if (!std::isfinite(src[a][e])) return fail(LQ2D_EINVAL, "non-finite input entry");
+  }
+  return create_common(out, K, N, T, n, m, src, cudaMemcpyHostToDevice, nullptr);
+}
+
+int lq2d_create_device(lq2d_problem** out, int K, int N, int T, int n, int m, const double* d_A_self,
+                       const double* d_A_nbr, const double* d_B, const double* d_Q, const double* d_R,
+                       const double* d_Q_T, const double* d_x0, void* stream) {
+  const double* src[7] = {d_A_self, d_A_nbr, d_B, d_Q, d_R, d_Q_T, d_x0};
+  return create_common(out, K, N, T, n, m, src, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+}
+
+int lq2d_update_device(lq2d_problem* h, const double* d_A_self, const double* d_A_nbr, const double* d_B,
+                       const double* d_Q, const double* d_R, const double* d_Q_T, const double* d_x0,
+                       void* stream) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  const double* src[7] = {d_A_self, d_A_nbr, d_B, d_Q, d_R, d_Q_T, d_x0};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = copy_inputs(h, src, cudaMemcpyDeviceToDevice, s);
+  if (rc) return rc;
+  return run_setup(h, s);
+}
+
+int lq2d_set_affine(lq2d_problem* h, const double* w) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  const Grid& g = h->g;
+  const size_t cnt = (size_t)g.T * g.NN * g.n;
+  if (w) {
+    for (size_t e = 0; e < cnt; ++e)
+      if (!std::isfinite(w[e])) return fail(LQ2D_EINVAL, "non-finite affine entry");
+    if (!h->w_buf) {
+      int rc = dev_alloc(h, &h->w_buf, cnt);
+      if (rc) return rc;
+    }
+    LQ_CUDA(cudaMemcpy(h->w_buf, w, cnt * sizeof(double), cudaMemcpyHostToDevice));
+    h->w_aff = h->w_buf;
+  } else {
+    h->w_aff = nullptr;
+  }
+  launch_build_rhs(g, h->sb.x0, h->w_aff, h->rhs, nullptr);
+  launch_norms(g, h->rhs, g.n, h->partials, &h->st->counters[kCntAux], h->bnorm, nullptr);
+  LQ_CUDA(cudaStreamSynchronize(nullptr));
+  LQ_CUDA(cudaGetLastError());
+  return LQ2D_OK;
+}
+
+int lq2d_solve(lq2d_problem* h, double tol, int S, int L, int max_iter, const double* delta0, double* x,
+               double* u, double* costate, int* iterations, double* rel_kkt) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  const Grid& g = h->g;
+  const size_t nx = (size_t)g.P * g.n, nu = (size_t)g.Pu * g.m;
+  const double* d_delta0 = nullptr;
+  if (delta0) {
+    LQ_CUDA(cudaMemcpy(h->stage_x, delta0, nx * sizeof(double), cudaMemcpyHostToDevice));
+    d_delta0 = h->stage_x;
+  }
+  // x goes through stage_x after delta0 has been consumed; costate through
+  // the same staging buffer after x has been copied out
+  int rc = solve_impl(h, tol, S, L, max_iter, d_delta0, nullptr, h->stage_u, nullptr, iterations, rel_kkt, nullptr);
+  if (rc != LQ2D_OK && rc != LQ2D_ENOCONV && rc != LQ2D_EBREAKDOWN) return rc;
+  std::string keep = g_err;
+  if (u) LQ_CUDA(cudaMemcpy(u, h->stage_u, nu * sizeof(double), cudaMemcpyDeviceToHost));
+  if (x) {
+    launch_to_api(h->z, h->stage_x, g.NN, g.T + 1, g.n, g.Ps, nullptr);
+    LQ_CUDA(cudaMemcpy(x, h->stage_x, nx * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (costate) {
+    launch_to_api(h->delta, h->stage_x, g.NN, g.T + 1, g.n, g.Ps, nullptr);
+    LQ_CUDA(cudaMemcpy(costate, h->stage_x, nx * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  g_err = keep;
+  return rc;
+}
+
+int lq2d_solve_device(lq2d_problem* h, double tol, int S, int L, int max_iter, const void* d_delta0, void* d_x,
+                      void* d_u, void* d_costate, int* iterations, double* rel_kkt, void* stream) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  return solve_impl(h, tol, S, L, max_iter, static_cast<const double*>(d_delta0), static_cast<double*>(d_x),
+                    static_cast<double*>(d_u), static_cast<double*>(d_costate), iterations, rel_kkt,
+                    static_cast<cudaStream_t>(stream));
+}
+
+int lq2d_apply_delta_device(lq2d_problem* h, const void* d_in, void* d_out, void* stream) {
+  if (!h || !d_in || !d_out) return fail(LQ2D_EINVAL, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Grid& g = h->g;
+  launch_to_internal(static_cast<const double*>(d_in), h->thA, g.NN, g.T + 1, g.n, g.Ps, s);
+  h->kt->delta_z(g, h->nd, h->thA, nullptr, h->z, nullptr, 0, s);
+  h->kt->delta_y(g, h->nd, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
+  launch_to_api(h->y, static_cast<double*>(d_out), g.NN, g.T + 1, g.n, g.Ps, s);
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  return LQ2D_OK;
+}
+
+int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, void* d_q, void* stream) {
+  if (!h || !d_r || !d_q) return fail(LQ2D_EINVAL, "null argument");
+  if (S < 1) return fail(LQ2D_EINVAL, "outer_S must be >= 1");
+  if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Grid& g = h->g;
+  launch_to_internal(static_cast<const double*>(d_r), h->y, g.NN, g.T + 1, g.n, g.Ps, s);
+  const double* q = enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
+  launch_to_api(q, static_cast<double*>(d_q), g.NN, g.T + 1, g.n, g.Ps, s);
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  return LQ2D_OK;
+}
+
+int lq2d_set_option(lq2d_problem* h, int option, double value) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  const int v = (int)value;
+  switch (option) {
+    case LQ2D_OPT_STOP_MODE:
+      if (v != 0 && v != 1) return fail(LQ2D_EINVAL, "stop mode must be 0 or 1");
+      h->stop_mode = v;
+      return LQ2D_OK;
+    case LQ2D_OPT_DRIVER:
+      if (v != 0 && v != 1) return fail(LQ2D_EINVAL, "driver must be 0 or 1");
+      h->driver = v;
+      return LQ2D_OK;
+    case LQ2D_OPT_TIMING:
+      h->timing = v ? 1 : 0;
+      return LQ2D_OK;
+    case LQ2D_OPT_MAX_RESTARTS:
+      if (v < 0) return fail(LQ2D_EINVAL, "max restarts must be >= 0");
+      h->max_restarts = v;
+      return LQ2D_OK;
+    default:
+      return fail(LQ2D_EINVAL, "unknown option");
+  }
+}
+
+int lq2d_get_stats(const lq2d_problem* h, lq2d_stats* out) {
+  if (!h || !out) return fail(LQ2D_EINVAL, "null argument");
+  *out = h->stats;
+  return LQ2D_OK;
+}
+
+int lq2d_set_precision(lq2d_problem* h, int mode) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  if (mode != 0) return fail(LQ2D_EINVAL, "unknown precision mode");
+  return LQ2D_OK;
+}
+
+void lq2d_destroy(lq2d_problem* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+const char* lq2d_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

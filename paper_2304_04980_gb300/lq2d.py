@@ -1,0 +1,221 @@
+"""ctypes binding of the lq2d C-ABI (include/lq2d.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Loading fails loudly when liblq2d.so has not been built; there is no CPU
+fallback.  Device buffers are anything with a ``data_ptr()`` (torch tensors)
+or a raw integer address; streams are ``torch.cuda.Stream`` objects, raw
+``cudaStream_t`` integers, or None for the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblq2d.so")
+
+OK, EINVAL, ENOTPD, ENOCONV, EBREAKDOWN, ECUDA, ENOMEM, ETIMEOUT = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ECUDA",
+                6: "ENOMEM", 7: "ETIMEOUT"}
+OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS = 1, 2, 3, 4
+
+EXPORTED = (
+    "lq2d_create", "lq2d_create_device", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
+    "lq2d_solve_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_set_option",
+    "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
+)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("status", ctypes.c_int),
+        ("sweep_launches", ctypes.c_int), ("delta_launches", ctypes.c_int), ("pad", ctypes.c_int),
+        ("rel_residual", ctypes.c_double), ("rel_kkt_residual", ctypes.c_double),
+        ("kkt_inf", ctypes.c_double), ("cost", ctypes.c_double),
+        ("sweep_ms", ctypes.c_double), ("delta_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
+
+class LQ2DError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def load() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblq2d.so not found at %s: build it with "
+                           "`python -m paper_2304_04980_gb300.build`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    i = ctypes.c_int
+    d = ctypes.c_double
+    pp = ctypes.POINTER(_vp)
+    sig = {
+        "lq2d_create": (i, [pp, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lq2d_create_device": (i, [pp, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lq2d_update_device": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lq2d_set_affine": (i, [_vp, _vp]),
+        "lq2d_solve": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp, _ip, _dp]),
+        "lq2d_solve_device": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp, _ip, _dp, _vp]),
+        "lq2d_apply_delta_device": (i, [_vp, _vp, _vp, _vp]),
+        "lq2d_apply_precond_device": (i, [_vp, i, i, _vp, _vp, _vp]),
+        "lq2d_set_option": (i, [_vp, i, d]),
+        "lq2d_get_stats": (i, [_vp, ctypes.POINTER(Stats)]),
+        "lq2d_set_precision": (i, [_vp, i]),
+        "lq2d_destroy": (None, [_vp]),
+        "lq2d_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().lq2d_last_error().decode()
+
+
+def _check(code: int, allow=()):
+    if code != OK and code not in allow:
+        raise LQ2DError(code, last_error())
+    return code
+
+
+def _addr(buf):
+    """Device or host address of a buffer (None -> NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not (buf.dtype == np.float64 and buf.flags.c_contiguous):
+            raise ValueError("host arrays must be C-contiguous float64")
+        return buf.ctypes.data
+    raise TypeError("unsupported buffer type %r" % type(buf))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _host(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Problem:
+    """One LQ problem on the GPU (handle of the C library)."""
+
+    def __init__(self, handle, K, N, T, n, m):
+        self._h = handle
+        self.K, self.N, self.T, self.n, self.m = K, N, T, n, m
+
+    # -- construction -----------------------------------------------------
+    @classmethod
+    def from_host(cls, K, N, T, n, m, A_self, A_nbr, B, Q, R, Q_T, x0):
+        lib = load()
+        arrs = [_host(a) for a in (A_self, A_nbr, B, Q, R, Q_T, x0)]
+        h = _vp()
+        _check(lib.lq2d_create(ctypes.byref(h), K, N, T, n, m, *[a.ctypes.data for a in arrs]))
+        return cls(h, K, N, T, n, m)
+
+    @classmethod
+    def from_device(cls, K, N, T, n, m, A_self, A_nbr, B, Q, R, Q_T, x0, stream=None):
+        lib = load()
+        h = _vp()
+        _check(lib.lq2d_create_device(ctypes.byref(h), K, N, T, n, m,
+                                      *[_addr(a) for a in (A_self, A_nbr, B, Q, R, Q_T, x0)],
+                                      _stream(stream)))
+        return cls(h, K, N, T, n, m)
+
+    @classmethod
+    def from_grid(cls, g):
+        """From a synth.GridLQ (host arrays)."""
+        return cls.from_host(g.K, g.N, g.T, g.n, g.m, *g.arrays())
+
+    def update_device(self, A_self, A_nbr, B, Q, R, Q_T, x0, stream=None):
+        _check(load().lq2d_update_device(self._h, *[_addr(a) for a in (A_self, A_nbr, B, Q, R, Q_T, x0)],
+                                         _stream(stream)))
+
+    def set_affine(self, w):
+        self._w = None if w is None else _host(w)
+        _check(load().lq2d_set_affine(self._h, None if w is None else self._w.ctypes.data))
+
+    # -- solves -----------------------------------------------------------
+    def solve(self, tol=1e-8, S=2, L=2, max_iter=10000, delta0=None, allow=(ENOCONV,)):
+        """Host solve; returns dict(x, u, costate, iterations, rel_kkt, status)."""
+        x = np.empty((self.T + 1, self.K * self.N, self.n))
+        u = np.empty((self.T, self.K * self.N, self.m))
+        lam = np.empty_like(x)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        d0 = None if delta0 is None else _host(delta0)
+        code = load().lq2d_solve(self._h, tol, S, L, max_iter, None if d0 is None else d0.ctypes.data,
+                                 x.ctypes.data, u.ctypes.data, lam.ctypes.data, ctypes.byref(it), ctypes.byref(rel))
+        _check(code, allow)
+        return dict(x=x, u=u, costate=lam, iterations=it.value, rel_kkt=rel.value, status=code)
+
+    def solve_device(self, tol, S, L, max_iter, delta0=None, x=None, u=None, costate=None, stream=None,
+                     allow=(ENOCONV,)):
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        code = load().lq2d_solve_device(self._h, tol, S, L, max_iter, _addr(delta0), _addr(x), _addr(u),
+                                        _addr(costate), ctypes.byref(it), ctypes.byref(rel), _stream(stream))
+        _check(code, allow)
+        return dict(iterations=it.value, rel_kkt=rel.value, status=code)
+
+    def apply_delta_device(self, d_in, d_out, stream=None):
+        _check(load().lq2d_apply_delta_device(self._h, _addr(d_in), _addr(d_out), _stream(stream)))
+
+    def apply_precond_device(self, S, L, d_r, d_q, stream=None):
+        _check(load().lq2d_apply_precond_device(self._h, S, L, _addr(d_r), _addr(d_q), _stream(stream)))
+
+    def set_option(self, option, value):
+        _check(load().lq2d_set_option(self._h, option, float(value)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().lq2d_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def set_precision(self, mode):
+        _check(load().lq2d_set_precision(self._h, mode))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().lq2d_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

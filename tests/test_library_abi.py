@@ -1,0 +1,78 @@
+"""CPU checks of the C-ABI library: it builds, loads without a GPU, exports
+every function declared in include/lq2d.h, and rejects bad arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lq2d.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_04980_gb300 import build, lq2d
+    build.build()
+    return lq2d.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lq2d_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_2304_04980_gb300 import lq2d
+    assert sorted(lq2d.EXPORTED) == declared_functions()
+
+
+def test_status_codes_match_header():
+    from paper_2304_04980_gb300 import lq2d
+    text = open(HEADER).read()
+    codes = dict(re.findall(r"LQ2D_(E[A-Z]+|OK)\s*=\s*(\d+)", text))
+    assert int(codes["OK"]) == lq2d.OK and int(codes["EINVAL"]) == lq2d.EINVAL
+    assert int(codes["ENOTPD"]) == lq2d.ENOTPD and int(codes["ETIMEOUT"]) == lq2d.ETIMEOUT
+
+
+def test_stats_struct_layout():
+    from paper_2304_04980_gb300 import lq2d
+    assert ctypes.sizeof(lq2d.Stats) == 6 * 4 + 6 * 8
+
+
+@pytest.mark.parametrize("dims", [(0, 4, 4, 2, 1), (4, 0, 4, 2, 1), (4, 4, 0, 2, 1), (4, 4, 4, 0, 1),
+                                  (4, 4, 4, 9, 1), (4, 4, 4, 2, 0), (4, 4, 4, 2, 9)])
+def test_bad_dimensions_rejected_without_gpu(lib, dims):
+    from paper_2304_04980_gb300 import lq2d
+    h = ctypes.c_void_p()
+    code = lib.lq2d_create(ctypes.byref(h), *dims, None, None, None, None, None, None, None)
+    assert code == lq2d.EINVAL and not h.value
+    assert lq2d.last_error()
+
+
+def test_non_finite_host_input_rejected_without_gpu(lib):
+    from paper_2304_04980_gb300 import lq2d, synth
+    g = synth.random_grid(2, 2, 3, 2, 1, seed=1)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in g.arrays()]
+    arrs[2] = arrs[2].copy()
+    arrs[2][0, 0, 0] = np.nan
+    h = ctypes.c_void_p()
+    code = lib.lq2d_create(ctypes.byref(h), g.K, g.N, g.T, g.n, g.m, *[a.ctypes.data for a in arrs])
+    assert code == lq2d.EINVAL and "non-finite" in lq2d.last_error()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2304_04980_gb300 import lq2d
+    assert lib.lq2d_solve(None, 1e-8, 2, 2, 10, None, None, None, None, None, None) == lq2d.EINVAL
+    assert lib.lq2d_set_option(None, 1, 0.0) == lq2d.EINVAL
+    lib.lq2d_destroy(None)
