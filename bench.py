@@ -1,0 +1,464 @@
+"""Benchmark of the lq2d solver: PCG iterations/s and time-to-solve at a
+1e-8 relative KKT residual, on the K = N = 64, n = 4, m = 2, T = 100
+synthetic grid (S = L = 2, FP64).
+
+One step = one full pass of the method over the resident problem: the setup
+(inverses, splitting blocks, banded block-Cholesky factors of Phi_bar), the
+PCG solve to the tolerance (Algorithm 1 with Algorithm 2 as
+preconditioner), and the recovery of x, u and the KKT residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+replica (the method has no data-path exchange on one GPU); value is the sum
+of iterations over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2304_04980_gb300 import synth  # noqa: E402
+
+METRIC = "PCG iters/s (time-to-solve at 1e-8 rel KKT residual)"
+UNIT = "iters/s"
+# FP64 peak of the GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x
+# 2.07 GHz (the nominal 1.25 TFLOP/s expressed in unit counts and clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="grid64_T100", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--driver", choices=["graph", "stream"], default="graph")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG steps in the CPU sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (replicas; the barrier and max are timing only)
+# --------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def reduce(self, value, op):
+        if self.pg is None:
+            return value
+        import torch
+        t = torch.tensor([float(value)], dtype=torch.float64,
+                         device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# clock sampling during the timed region
+# --------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic flop model of one NBJM sweep (FP64 path)
+# --------------------------------------------------------------------------
+
+def band_solve_flops(K, n, cols):
+    """Forward plus backward substitution with the banded block-Cholesky
+    factor of one Phi_bar_{v,t} block (Section IV-B), envelope entries only:
+    each multiply-add counts 2 flops, each diagonal scaling 1."""
+    f = 0
+    for i in range(K):
+        for a in range(cols * n):
+            e = a
+            if i >= 1:
+                e += cols * n
+            if i >= 2:
+                e += (2 * n if a < n else n) if cols == 2 else n
+            f += 2 * e + 1
+    return 2 * f
+
+
+def sweep_flops(g: synth.GridLQ):
+    """Algorithmic flops of one sweep launch of each kind, keyed by variant."""
+    K, N, T, n = g.K, g.N, g.T, g.n
+    V = (N + 1) // 2
+    pairs_two = N // 2
+    pairs_one = V - pairs_two
+    band = T * (pairs_two * band_solve_flops(K, n, 2) + pairs_one * band_solve_flops(K, n, 1))
+    t0 = K * N * 2 * n * n                      # theta_0 = Q tau, node by node
+    # valid neighbour counts
+    offpair = 0
+    nbrs = 0
+    for i in range(K):
+        for j in range(N):
+            s = 1 if (j % 2) else -1
+            cand = [(i, j + s), (i - 1, j + s), (i + 1, j + s), (i, j + 2 * s), (i, j - 2 * s)]
+            offpair += sum(0 <= a < K and 0 <= b < N for a, b in cand)
+            nbrs += 1 + sum(0 <= a < K and 0 <= b < N for a, b in ((i, j - 1), (i, j + 1), (i - 1, j), (i + 1, j)))
+    omega = T * offpair * 2 * n * n
+    xi = 2 * T * nbrs * 2 * n * n               # A Q^-1 delta_{t-1} for t >= 1, Q^-1 A' delta_{t+1} for t < T
+    unknowns = K * N * (T + 1) * n
+    return {
+        "update": band + t0 + 6 * unknowns,
+        "omega": band + t0 + omega,
+        "omega_mu": band + t0 + omega + 2 * unknowns,
+        "xi": band + t0 + xi,
+        "plain": band + t0,
+    }
+
+
+def sweep_flops_of_solve(fl, iterations, S=2, L=2):
+    """Flops of the sweep launches timed in one solve: every PCG step but the
+    last runs update, omega, xi, omega_mu (S = L = 2); the last one stops
+    after the update sweep."""
+    assert S == 2 and L == 2
+    full = fl["update"] + fl["omega"] + fl["xi"] + fl["omega_mu"]
+    return max(iterations - 1, 0) * full + (fl["update"] if iterations > 0 else 0)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels_hot.cuh", "common.cuh", "kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2304_04980_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "nbjm_sweep_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram bytes per launch \(read\+write\):\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, single-threaded, bounded sample
+# --------------------------------------------------------------------------
+
+CPU_SCRIPT = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+from oracle import lq2d_oracle as O
+from paper_2304_04980_gb300 import synth
+g = synth.workload(%(workload)r)
+t0 = time.perf_counter()
+orc = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays()))
+pre = orc.preconditioner(2, 2)
+t1 = time.perf_counter()
+res = O.pcg(orc.Delta, orc.r_delta, pre.apply, 1e-300, %(iters)d, confirm_true_residual=False)
+t2 = time.perf_counter()
+print(json.dumps({"setup_s": t1 - t0, "iters": res.iterations, "loop_s": t2 - t1}))
+"""
+
+
+def cpu_baseline(workload, iters):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = CPU_SCRIPT % {"root": ROOT, "workload": workload, "iters": iters}
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + out.stderr.strip().splitlines()[-1][:200] if out.stderr else "failed"}
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": r["iters"] / r["loop_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d PCG steps (Algorithm 1 loop, S=L=2) of the oracle on the full %s problem, "
+                      "single thread; oracle setup (assembly, splitting, banded Cholesky) %.1f s not counted"
+                      % (r["iters"], workload, r["setup_s"]),
+            "setup_s": r["setup_s"], "loop_s": r["loop_s"]}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle timed on the host cores
+# --------------------------------------------------------------------------
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    from oracle import lq2d_oracle as O
+    g = synth.workload(args.workload)
+    orc = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays()))
+    pre = orc.preconditioner(2, 2)
+    per_step = 2
+
+    def step():
+        res = O.pcg(orc.Delta, orc.r_delta, pre.apply, 1e-300, per_step, confirm_true_residual=False)
+        return res.iterations
+
+    for _ in range(args.warmup):
+        O.pcg(orc.Delta, orc.r_delta, pre.apply, 1e-300, 1, confirm_true_residual=False)
+    t0 = time.perf_counter()
+    its = sum(step() for _ in range(args.steps))
+    t1 = time.perf_counter()
+    value = its / (t1 - t0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": (t1 - t0) * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "K": g.K, "N": g.N, "T": g.T, "n": g.n, "m": g.m, "S": 2, "L": 2,
+                   "tol": args.tol, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step = %d PCG steps of the CPU oracle (numpy/scipy, as it stands) on the "
+                                   "full problem; oracle setup not timed" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, dist):
+    import torch
+
+    from paper_2304_04980_gb300 import lq2d
+
+    lq2d.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    g = synth.workload(args.workload)
+    host = [np.ascontiguousarray(a) for a in g.arrays()]
+    inputs = [torch.from_numpy(a).to(dev) for a in host]
+    pinned = [torch.from_numpy(a).pin_memory() for a in host]
+    prob = lq2d.Problem.from_device(g.K, g.N, g.T, g.n, g.m, *inputs, stream=stream)
+    if args.driver == "stream":
+        prob.set_option(lq2d.OPT_DRIVER, 1)
+    x = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
+    u = torch.empty((g.T, g.nodes, g.m), dtype=torch.float64, device=dev)
+    lam = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    max_iter = 100000
+
+    def step():
+        prob.update_device(*inputs, stream=stream)
+        out = prob.solve_device(args.tol, 2, 2, max_iter, x=x, u=u, costate=lam, stream=stream)
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, device events per step
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = Clocks(uuid)
+    launches0 = prob.stats()["launches_total"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters, rels = [], []
+    clocks.start()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        out = step()
+        evs[k][1].record(stream)
+        iters.append(out["iterations"])
+        rels.append(out["rel_kkt"])
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    w1 = time.perf_counter()
+    clk = clocks.stop()
+    launches = prob.stats()["launches_total"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_ms = sum(step_ms)
+    tot_iters = sum(iters)
+    all_iters = dist.reduce(tot_iters, "sum")
+    max_ms = dist.reduce(dev_ms, "max")
+    value = all_iters / (max_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (NBJM sweep): per-launch events on
+    # the solve stream, over the same K steps run again with timing on
+    prob.set_option(lq2d.OPT_TIMING, 1)
+    sweep_ms, sweep_launches, delta_ms, delta_launches, fl_total, it_r = 0.0, 0, 0.0, 0, 0, 0
+    fl = sweep_flops(g)
+    for _ in range(args.steps):
+        flush.zero_()
+        out = step()
+        st = prob.stats()
+        sweep_ms += st["sweep_ms"]
+        sweep_launches += st["sweep_launches"]
+        delta_ms += st["delta_ms"]
+        delta_launches += st["delta_launches"]
+        fl_total += sweep_flops_of_solve(fl, out["iterations"])
+        it_r += out["iterations"]
+    prob.set_option(lq2d.OPT_TIMING, 0)
+    achieved = fl_total / (sweep_ms / 1e3) / 1e12
+    roofline = {
+        "kernel": "nbjm_sweep_kernel<4,*>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+        "traffic": profiled_traffic(args.workload),
+        "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
+        "flops_per_launch": fl_total / max(sweep_launches, 1),
+        "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+        "measured": "CUDA events around each sweep launch on the solve stream, second pass over the same %d steps"
+                    % args.steps,
+        "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
+    }
+
+    # ---- end to end: host (pinned) inputs in, host outputs back, per step
+    xh = np.empty((g.T + 1, g.nodes, g.n))
+    uh = np.empty((g.T, g.nodes, g.m))
+    lh = np.empty_like(xh)
+    h2d = sum(a.nbytes for a in host)
+    d2h = xh.nbytes + uh.nbytes + lh.nbytes
+    torch.cuda.synchronize()
+    e_iters = 0
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        prob.update(*[p.data_ptr() for p in pinned])
+        out = prob.solve(args.tol, 2, 2, max_iter, out=(xh, uh, lh))
+        e_iters += out["iterations"]
+    e1 = time.perf_counter()
+    e2e_value = dist.reduce(e_iters, "sum") / dist.reduce(e1 - e0, "max")
+    prob.close()
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, args.cpu_iters)
+
+    if dist.rank == 0:
+        mean_iters = tot_iters / len(iters)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "K": g.K, "N": g.N, "T": g.T, "n": g.n, "m": g.m, "S": 2,
+                       "L": 2, "tol": args.tol, "precision": "fp64", "driver": args.driver,
+                       "l2": "flushed before each step (256 MiB write, outside the step events)",
+                       "parallelism": "replicas" if dist.world > 1 else "single"},
+            "time_to_solve_ms": dev_ms / args.steps,
+            "iterations_per_solve": mean_iters,
+            "rel_kkt_residual": max(rels),
+            "wall_ms": (w1 - w0) * 1e3,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)   # rank 0 only; no process group needed
+        return
+    import torch
+    if dist.world > 1:
+        torch.cuda.set_device(dist.local)
+    dist.init("nccl")
+    try:
+        run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -83,6 +83,9 @@ typedef struct lq2d_stats {
   double cost;             /* 1/2 (x'Q~x + u'R~u) */
   double sweep_ms;         /* summed device time of the timed sweep launches */
   double delta_ms;         /* summed device time of the timed Delta-apply launches */
+  long long launches_total; /* kernels launched for this handle since creation (setup included) */
+  int body_executions;     /* device-loop body executions in the last solve */
+  int pad2;
 } lq2d_stats;
 
 /* Creates a problem from host arrays, copies them to the current device and
@@ -116,6 +119,11 @@ int lq2d_create_device(lq2d_problem **out, int K, int N, int T, int n, int m,
 int lq2d_update_device(lq2d_problem *h, const double *d_A_self, const double *d_A_nbr,
                        const double *d_B, const double *d_Q, const double *d_R,
                        const double *d_Q_T, const double *d_x0, void *stream);
+
+/* As lq2d_update_device with host arrays (copied to the device, then the
+ * setup is re-run).  Allocates no device memory. */
+int lq2d_update(lq2d_problem *h, const double *A_self, const double *A_nbr, const double *B,
+                const double *Q, const double *R, const double *Q_T, const double *x0);
 
 /* Boundary/affine terms omega_t (Section II-A: M_hat alpha + N_hat beta),
  * host array [T][K*N][n] entering x_{t+1} = ... + omega_t; NULL clears them. */

@@ -131,8 +131,14 @@ def grid_dynamics_matrix(P: Problem) -> sp.csr_matrix:
 
 
 def block_diag_sparse(blocks: np.ndarray) -> sp.csr_matrix:
-    """blkdiag(blocks[0], blocks[1], ...) for a stack of equal square blocks."""
-    return sp.csr_matrix(sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr"))
+    """blkdiag(blocks[0], blocks[1], ...) for a stack of equal-shape blocks:
+    entry (r, c) of block b sits at (b*rows + r, b*cols + c)."""
+    nb, r, c = blocks.shape
+    rows = np.broadcast_to(np.arange(nb)[:, None, None] * r + np.arange(r)[None, :, None], blocks.shape)
+    cols = np.broadcast_to(np.arange(nb)[:, None, None] * c + np.arange(c)[None, None, :], blocks.shape)
+    M = sp.csr_matrix((blocks.ravel(), (rows.ravel(), cols.ravel())), shape=(nb * r, nb * c))
+    M.eliminate_zeros()
+    return M
 
 
 def blockwise_inverse(blocks: np.ndarray) -> np.ndarray:
@@ -559,7 +565,7 @@ def delta_rows_matrix_free(P: Problem, rows: np.ndarray, vec: np.ndarray) -> np.
         zt = z(t)
         val = -zt[rem]
         if t >= 1:
-            val += Ahat[rem] @ z(t - 1)
+            val += float((Ahat[rem] @ z(t - 1))[0])
             p, k = divmod(rem, n)
             val += Sblk[p, k] @ V[t, p * n:(p + 1) * n]
         out[o] = val

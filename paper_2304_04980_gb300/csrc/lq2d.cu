@@ -74,6 +74,8 @@ struct lq2d_problem {
   int ngraphs = 0;
   lq2d_stats stats{};
   std::vector<cudaEvent_t> ev_pool;
+  long long launches = 0;  // kernels launched on behalf of this handle since creation
+  int graph_body_kernels = 0;  // kernels per device-loop body of the last graph launch (0: no graph)
 };
 
 namespace {
@@ -198,6 +200,7 @@ int run_setup(lq2d_problem* h, cudaStream_t s) {
   launch_setup(h->sb, g.K, g.N, g.n, g.m, g.V, h->nd.fac_rec, h->nd.fac_vc, h->setup_status, s);
   launch_build_rhs(g, h->sb.x0, h->w_aff, h->rhs, s);
   launch_norms(g, h->rhs, g.n, h->partials, &h->st->counters[kCntAux], h->bnorm, s);
+  h->launches += 7;
   LQ_CUDA(cudaMemcpyAsync(&h->h_done[0], h->setup_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
@@ -285,6 +288,7 @@ const double* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, b
         cudaEventRecord(e0, s);
       }
       h->kt->sweep(variant, h->g, h->nd, a, st, s);
+      h->launches += 1;
       if (timing) cudaEventRecord(e1, s);
       prev = bufs[out_i];
       out_i ^= 1;
@@ -308,6 +312,7 @@ void enqueue_delta(lq2d_problem* h, const double* q, const double* dold, double*
   }
   h->kt->delta_z(h->g, h->nd, q, dold, h->z, st, loop ? 1 : 0, s);
   h->kt->delta_y(h->g, h->nd, h->z, q, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+  h->launches += 2;
   if (timing) cudaEventRecord(e1, s);
 }
 
@@ -349,7 +354,9 @@ int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   LQ_CUDA(cudaGraphAddNode(&node, ge.graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   LQ_CUDA(cudaStreamBeginCaptureToGraph(h->priv, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const long long before = h->launches;
   enqueue_step(h, S, L, h->priv, false);
+  h->launches = before;  // captured, not launched: body executions are counted after each solve
   launch_loop_ctrl(h->st, hc, h->priv);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(h->priv, &captured);
@@ -374,6 +381,7 @@ int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
     int rc = get_graph(h, S, L, &exec);
     if (rc) return rc;
     LQ_CUDA(cudaGraphLaunch(exec, s));
+    h->graph_body_kernels = 2 + S * L + 1;
     return LQ2D_OK;
   }
   // driver 1: steps enqueued from the host in chunks; the stop flag of the
@@ -445,7 +453,9 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
   std::memset(&h->stats, 0, sizeof(h->stats));
   h->ev_pool.clear();
   launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, s);
+  h->launches += 2;  // state and initial residual
   if (d_delta0) {
+    h->launches += 3;
     launch_to_internal(d_delta0, h->thA, g.NN, g.T + 1, g.n, g.Ps, s);
     kt->delta_z(g, h->nd, h->thA, nullptr, h->z, nullptr, 0, s);
     kt->delta_y(g, h->nd, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
@@ -460,8 +470,10 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
   for (;;) {
     enqueue_precond(h, S, L, false, true, h->st, h->r, s, false);
     LQ_CUDA(cudaMemsetAsync(h->d, 0, (size_t)g.Ps * g.n * sizeof(double), s));
+    h->graph_body_kernels = 0;
     int rc = run_loop(h, S, L, max_iter, s);
     if (rc) return rc;
+    h->launches += 3;  // recovery
     // recovery (Section II-B): x = Q~^-1 A~' delta into z, u = R~^-1 B~' delta,
     // and the full KKT residual of (x, u, delta)
     kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
@@ -472,6 +484,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     LQ_CUDA(cudaStreamSynchronize(s));
     LQ_CUDA(cudaGetLastError());
     const SolverState& hs = *h->h_st;
+    h->launches += (long long)hs.body_count * h->graph_body_kernels;
     if (h->timing) collect_timing(h, S, L, hs.iter - iter_before);
     iter_before = hs.iter;
     const double bn = std::sqrt(hs.bnorm2);
@@ -481,6 +494,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
       // the recurrence residual passed but the true one did not: restart
       // from the current iterate with r = r_delta - Delta delta
       ++restarts;
+      h->launches += 4;
       launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 1, s);
       kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
       kt->delta_y(g, h->nd, h->z, h->delta, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
@@ -501,11 +515,13 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     h->stats.kkt_inf = h->h_kkt[2];
     h->stats.cost = 0.5 * h->h_kkt[1];
     h->stats.status = status;
+    h->stats.body_executions = hs.body_count;
     break;
   }
   if (d_x) launch_to_api(h->z, d_x, g.NN, g.T + 1, g.n, g.Ps, s);
   if (d_u) launch_to_api(h->u, d_u, g.NN, g.T, g.m, g.Pus, s);
   if (d_costate) launch_to_api(h->delta, d_costate, g.NN, g.T + 1, g.n, g.Ps, s);
+  h->launches += (d_x != nullptr) + (d_u != nullptr) + (d_costate != nullptr);
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
   if (iterations) *iterations = h->stats.iterations;
@@ -555,6 +571,23 @@ int lq2d_update_device(lq2d_problem* h, const double* d_A_self, const double* d_
   return run_setup(h, s);
 }
 
+int lq2d_update(lq2d_problem* h, const double* A_self, const double* A_nbr, const double* B, const double* Q,
+                const double* R, const double* Q_T, const double* x0) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  const double* src[7] = {A_self, A_nbr, B, Q, R, Q_T, x0};
+  const Grid& g = h->g;
+  const size_t NN = g.NN, n = g.n, m = g.m;
+  const size_t cnt[7] = {NN * n * n, NN * 4 * n * n, NN * n * m, NN * n * n, NN * m * m, NN * n * n, NN * n};
+  for (int a = 0; a < 7; ++a) {
+    if (!src[a]) return fail(LQ2D_EINVAL, "null input array");
+    for (size_t e = 0; e < cnt[a]; ++e)
+      if (!std::isfinite(src[a][e])) return fail(LQ2D_EINVAL, "non-finite input entry");
+  }
+  int rc = copy_inputs(h, src, cudaMemcpyHostToDevice, nullptr);
+  if (rc) return rc;
+  return run_setup(h, nullptr);
+}
+
 int lq2d_set_affine(lq2d_problem* h, const double* w) {
   if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
   const Grid& g = h->g;
@@ -573,6 +606,7 @@ int lq2d_set_affine(lq2d_problem* h, const double* w) {
   }
   launch_build_rhs(g, h->sb.x0, h->w_aff, h->rhs, nullptr);
   launch_norms(g, h->rhs, g.n, h->partials, &h->st->counters[kCntAux], h->bnorm, nullptr);
+  h->launches += 2;
   LQ_CUDA(cudaStreamSynchronize(nullptr));
   LQ_CUDA(cudaGetLastError());
   return LQ2D_OK;
@@ -595,10 +629,12 @@ int lq2d_solve(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
   std::string keep = g_err;
   if (u) LQ_CUDA(cudaMemcpy(u, h->stage_u, nu * sizeof(double), cudaMemcpyDeviceToHost));
   if (x) {
+    h->launches += 1;
     launch_to_api(h->z, h->stage_x, g.NN, g.T + 1, g.n, g.Ps, nullptr);
     LQ_CUDA(cudaMemcpy(x, h->stage_x, nx * sizeof(double), cudaMemcpyDeviceToHost));
   }
   if (costate) {
+    h->launches += 1;
     launch_to_api(h->delta, h->stage_x, g.NN, g.T + 1, g.n, g.Ps, nullptr);
     LQ_CUDA(cudaMemcpy(costate, h->stage_x, nx * sizeof(double), cudaMemcpyDeviceToHost));
   }
@@ -618,6 +654,7 @@ int lq2d_apply_delta_device(lq2d_problem* h, const void* d_in, void* d_out, void
   if (!h || !d_in || !d_out) return fail(LQ2D_EINVAL, "null argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Grid& g = h->g;
+  h->launches += 4;
   launch_to_internal(static_cast<const double*>(d_in), h->thA, g.NN, g.T + 1, g.n, g.Ps, s);
   h->kt->delta_z(g, h->nd, h->thA, nullptr, h->z, nullptr, 0, s);
   h->kt->delta_y(g, h->nd, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
@@ -633,6 +670,7 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
   if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Grid& g = h->g;
+  h->launches += 2;
   launch_to_internal(static_cast<const double*>(d_r), h->y, g.NN, g.T + 1, g.n, g.Ps, s);
   const double* q = enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
   launch_to_api(q, static_cast<double*>(d_q), g.NN, g.T + 1, g.n, g.Ps, s);
@@ -668,6 +706,7 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
 int lq2d_get_stats(const lq2d_problem* h, lq2d_stats* out) {
   if (!h || !out) return fail(LQ2D_EINVAL, "null argument");
   *out = h->stats;
+  out->launches_total = h->launches;
   return LQ2D_OK;
 }
 

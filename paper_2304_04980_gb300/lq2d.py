@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "EBREAKDOWN"
 OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS = 1, 2, 3, 4
 
 EXPORTED = (
-    "lq2d_create", "lq2d_create_device", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
+    "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
     "lq2d_solve_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
 )
@@ -35,10 +35,11 @@ class Stats(ctypes.Structure):
         ("rel_residual", ctypes.c_double), ("rel_kkt_residual", ctypes.c_double),
         ("kkt_inf", ctypes.c_double), ("cost", ctypes.c_double),
         ("sweep_ms", ctypes.c_double), ("delta_ms", ctypes.c_double),
+        ("launches_total", ctypes.c_longlong), ("body_executions", ctypes.c_int), ("pad2", ctypes.c_int),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+        return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("pad")}
 
 
 class LQ2DError(RuntimeError):
@@ -68,6 +69,7 @@ def load() -> ctypes.CDLL:
     sig = {
         "lq2d_create": (i, [pp, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lq2d_create_device": (i, [pp, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lq2d_update": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lq2d_update_device": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lq2d_set_affine": (i, [_vp, _vp]),
         "lq2d_solve": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp, _ip, _dp]),
@@ -155,6 +157,12 @@ class Problem:
         """From a synth.GridLQ (host arrays)."""
         return cls.from_host(g.K, g.N, g.T, g.n, g.m, *g.arrays())
 
+    def update(self, A_self, A_nbr, B, Q, R, Q_T, x0):
+        """Host arrays (numpy, or pinned host tensors via their address)."""
+        args = [a if isinstance(a, int) or hasattr(a, "data_ptr") else _host(a)
+                for a in (A_self, A_nbr, B, Q, R, Q_T, x0)]
+        _check(load().lq2d_update(self._h, *[_addr(a) for a in args]))
+
     def update_device(self, A_self, A_nbr, B, Q, R, Q_T, x0, stream=None):
         _check(load().lq2d_update_device(self._h, *[_addr(a) for a in (A_self, A_nbr, B, Q, R, Q_T, x0)],
                                          _stream(stream)))
@@ -164,11 +172,15 @@ class Problem:
         _check(load().lq2d_set_affine(self._h, None if w is None else self._w.ctypes.data))
 
     # -- solves -----------------------------------------------------------
-    def solve(self, tol=1e-8, S=2, L=2, max_iter=10000, delta0=None, allow=(ENOCONV,)):
-        """Host solve; returns dict(x, u, costate, iterations, rel_kkt, status)."""
-        x = np.empty((self.T + 1, self.K * self.N, self.n))
-        u = np.empty((self.T, self.K * self.N, self.m))
-        lam = np.empty_like(x)
+    def solve(self, tol=1e-8, S=2, L=2, max_iter=10000, delta0=None, allow=(ENOCONV,), out=None):
+        """Host solve; returns dict(x, u, costate, iterations, rel_kkt, status).
+        `out` = (x, u, costate) preallocated float64 arrays, else new ones."""
+        if out is None:
+            x = np.empty((self.T + 1, self.K * self.N, self.n))
+            u = np.empty((self.T, self.K * self.N, self.m))
+            lam = np.empty_like(x)
+        else:
+            x, u, lam = out
         it = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
         d0 = None if delta0 is None else _host(delta0)

@@ -115,6 +115,8 @@ WORKLOADS = {
     "grid4_T20": dict(kind="random", K=4, N=4, T=20, n=2, m=1, seed=0, tol=1e-10),
     "grid64_T100": dict(kind="diffusion", K=64, N=64, T=100, n=4, m=2, seed=1, tol=1e-8),
     "grid256_T200": dict(kind="random", K=256, N=256, T=200, n=4, m=2, seed=2, tol=1e-8),
+    # profiling size: vectors of 52 MB, so one sweep's traffic exceeds the L2
+    "grid128_T100": dict(kind="random", K=128, N=128, T=100, n=4, m=2, seed=3, tol=1e-8),
 }
 
 

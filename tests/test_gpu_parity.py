@@ -294,3 +294,17 @@ def test_full_size_solve_properties(dev, big):
     rd[: g.nodes * g.n] = -g.x0.ravel()
     res = rd[rows] - O.delta_rows_matrix_free(P, rows, out["costate"].ravel())
     assert np.abs(res).max() <= 1e-9 * np.linalg.norm(rd)
+
+
+def test_full_size_solution_matches_oracle(dev, big):
+    """The whole K = N = 64, T = 100 solve against the oracle's PCG, both run
+    to 1e-11: relative solution error within the FP64 target 1e-8."""
+    g, prob = big
+    orc = oracle_for(g)
+    ref = orc.solve(1e-11, 2, 2, max_iter=2000)
+    out = prob.solve(1e-11, 2, 2, 2000)
+    assert ref.converged and out["status"] == 0
+    assert rel_err(out["costate"], ref.delta) <= 1e-8
+    assert rel_err(out["x"], ref.x) <= 1e-8
+    assert rel_err(out["u"], ref.u) <= 1e-8
+    assert abs(out["iterations"] - ref.iterations) <= max(2, 0.05 * ref.iterations)

@@ -334,3 +334,16 @@ def test_absolute_infinity_norm_stop():
     sol = orc.solve(1e-9, stop="absinf")
     r = orc.r_delta - orc.Delta @ sol.delta.ravel()
     assert np.max(np.abs(r)) < 1e-9 * 1.01
+
+
+def test_row_evaluation_matches_assembled_delta():
+    """The row-by-row evaluation used for sampled checks at large sizes
+    equals the rows of the assembled Delta (below eq. kkt_conditions)."""
+    g = synth.random_grid(4, 5, 6, 3, 2, seed=81)
+    P = as_problem(g)
+    orc = O.Oracle(P)
+    v = synth.random_vector(P.dim_x, seed=3)
+    rows = np.arange(P.dim_x)
+    got = O.delta_rows_matrix_free(P, rows, v)
+    ref = orc.Delta @ v
+    assert np.allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
