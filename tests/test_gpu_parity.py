@@ -276,9 +276,13 @@ def test_full_size_solve_properties(dev, big):
     g, prob = big
     out = prob.solve(1e-10, 2, 2, 5000)
     assert out["status"] == 0 and out["rel_kkt"] <= 1e-10
-    # the inputs reproduce the states through the dynamics
-    x_sim = grid_sim.simulate(g.K, g.N, g.T, g.A_self, g.A_nbr, g.B, g.x0, out["u"])
-    assert rel_err(x_sim, out["x"]) <= 1e-8
+    # every step of (x, u) satisfies the dynamics (checked one step at a
+    # time: the open-loop dynamics of this workload are unstable, so a
+    # forward simulation would amplify the 1e-10 residual)
+    assert np.array_equal(out["x"][0], g.x0)
+    step_res = [out["x"][t + 1] - grid_sim.step(g.K, g.N, g.A_self, g.A_nbr, g.B, out["x"][t], out["u"][t])
+                for t in range(g.T)]
+    assert np.linalg.norm(np.array(step_res)) <= 1e-9 * np.linalg.norm(g.x0)
     # terminal costate: delta_T = -Q_T x_T (reading A3)
     lamT = -np.einsum("pab,pb->pa", g.Q_T, out["x"][-1])
     assert rel_err(out["costate"][-1], lamT) <= 1e-12
