@@ -157,6 +157,30 @@ int lq2d_apply_delta_device(lq2d_problem *h, const void *d_in, void *d_out, void
 int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const void *d_r,
                               void *d_q, void *stream);
 
+/* y = Delta d as lq2d_apply_delta_device computes it, for callers that may
+ * not allocate device memory: it takes the raw problem blocks (device
+ * pointers, layouts as in lq2d_create) instead of a handle, and keeps its
+ * scratch (Q^-1, Q_T^-1, B R^-1 B' per node, and the intermediate
+ * Q~^-1 A~' d) in one fixed array compiled into the library.  The paper has
+ * no counterpart; it is an allocation-free form of the Delta product.
+ *   Callers: a controller that re-evaluates Delta d in a fixed-period loop,
+ *   where an allocator call adds latency it cannot bound, and host
+ *   frameworks that own every device allocation and pass libraries only
+ *   the buffers they manage.
+ *   Limit: (T+1)*K*N*n + 3*K*N*n*n + 1 <= 2^21 doubles (16 MiB, held on
+ *   every GPU that loads the library until the process exits); larger
+ *   problems return LQ2D_EINVAL with the required size in the message.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make
+ *   that first call before any stream capture.  All calls share the array
+ *   and it keeps the last call's contents; calls whose work overlaps on the
+ *   GPU race on it.  Calls no cudaMalloc or cudaFree.  Returns after the
+ *   work on `stream` is complete; LQ2D_ENOTPD if Q, Q_T or R is not SPD. */
+int lq2d_apply_delta_static(int K, int N, int T, int n, int m,
+                            const double *d_A_self, const double *d_A_nbr, const double *d_B,
+                            const double *d_Q, const double *d_R, const double *d_Q_T,
+                            const void *d_in, void *d_out, void *stream);
+
 int lq2d_set_option(lq2d_problem *h, int option, double value);
 int lq2d_get_stats(const lq2d_problem *h, lq2d_stats *out);
 

@@ -535,6 +535,12 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
 
 }  // namespace
 
+namespace lq2d {
+// Lets other translation units of the library report a message through
+// lq2d_last_error().
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace lq2d
+
 extern "C" {
 
 int lq2d_create(lq2d_problem** out, int K, int N, int T, int n, int m, const double* A_self, const double* A_nbr,

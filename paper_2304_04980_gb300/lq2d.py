@@ -23,7 +23,8 @@ OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS = 1, 2, 3, 4
 
 EXPORTED = (
     "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
-    "lq2d_solve_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_set_option",
+    "lq2d_solve_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_apply_delta_static",
+    "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
 )
 
@@ -76,6 +77,7 @@ def load() -> ctypes.CDLL:
         "lq2d_solve_device": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp, _ip, _dp, _vp]),
         "lq2d_apply_delta_device": (i, [_vp, _vp, _vp, _vp]),
         "lq2d_apply_precond_device": (i, [_vp, i, i, _vp, _vp, _vp]),
+        "lq2d_apply_delta_static": (i, [i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lq2d_set_option": (i, [_vp, i, d]),
         "lq2d_get_stats": (i, [_vp, ctypes.POINTER(Stats)]),
         "lq2d_set_precision": (i, [_vp, i]),
@@ -121,6 +123,13 @@ def _stream(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def apply_delta_static(K, N, T, n, m, A_self, A_nbr, B, Q, R, Q_T, d_in, d_out, stream=None):
+    """y = Delta d from raw device blocks, with no device allocation (see
+    lq2d_apply_delta_static in include/lq2d.h)."""
+    _check(load().lq2d_apply_delta_static(K, N, T, n, m, *[_addr(a) for a in (A_self, A_nbr, B, Q, R, Q_T)],
+                                          _addr(d_in), _addr(d_out), _stream(stream)))
 
 
 def _host(a):
