@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--workload", default="grid64_T100", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--driver", choices=["graph", "stream"], default="graph")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="fp64: FP64 everywhere; mixed: FP32 preconditioner, FP64 residual/dots/updates")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the timed mixed-precision comparison on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG steps in the CPU sample")
     return ap.parse_args()
@@ -193,6 +197,20 @@ def sweep_flops(g: synth.GridLQ):
     }
 
 
+# Algorithmic bytes per unknown of each FP32 sweep of the mixed mode: every
+# vector operand read once and every result written once (r, delta, y, d and
+# r_theta are FP64; theta and delta^(s) FP32); factors and node blocks are
+# time-invariant, L2-resident and amortised over the T+1 time slices.
+MIXED_SWEEP_BYTES = {"update": 4 * 8 + 2 * 8 + 4, "omega": 8 + 4 + 4, "xi": 8 + 4 + 8 + 4,
+                     "omega_mu": 8 + 4 + 4 + 8 + 8}
+
+
+def sweep_bytes_of_solve(g, iterations):
+    unknowns = g.nodes * (g.T + 1) * g.n
+    full = sum(MIXED_SWEEP_BYTES.values()) * unknowns
+    return max(iterations - 1, 0) * full + (MIXED_SWEEP_BYTES["update"] * unknowns if iterations > 0 else 0)
+
+
 def sweep_flops_of_solve(fl, iterations, S=2, L=2):
     """Flops of the sweep launches timed in one solve: every PCG step but the
     last runs update, omega, xi, omega_mu (S = L = 2); the last one stops
@@ -200,6 +218,16 @@ def sweep_flops_of_solve(fl, iterations, S=2, L=2):
     assert S == 2 and L == 2
     full = fl["update"] + fl["omega"] + fl["xi"] + fl["omega_mu"]
     return max(iterations - 1, 0) * full + (fl["update"] if iterations > 0 else 0)
+
+
+def measured_hbm_gbs():
+    """The measured copy bandwidth of the GB300s (GB/s), else
+    the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def kernel_source_hash():
@@ -316,6 +344,8 @@ def run_ours(args, dist):
     inputs = [torch.from_numpy(a).to(dev) for a in host]
     pinned = [torch.from_numpy(a).pin_memory() for a in host]
     prob = lq2d.Problem.from_device(g.K, g.N, g.T, g.n, g.m, *inputs, stream=stream)
+    if args.precision == "mixed":
+        prob.set_precision(1)
     if args.driver == "stream":
         prob.set_option(lq2d.OPT_DRIVER, 1)
     x = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
@@ -333,6 +363,19 @@ def run_ours(args, dist):
         step()
     torch.cuda.synchronize()
 
+    def timed(nsteps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        its, rls = [], []
+        for k in range(nsteps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            out = step()
+            evs[k][1].record(stream)
+            its.append(out["iterations"])
+            rls.append(out["rel_kkt"])
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs], its, rls
+
     # ---- timed region: K steps, L2 flushed before each, device events per step
     uuid = None
     try:
@@ -342,27 +385,17 @@ def run_ours(args, dist):
         uuid = None
     clocks = Clocks(uuid)
     launches0 = prob.stats()["launches_total"]
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters, rels = [], []
     clocks.start()
     torch.cuda.synchronize()
     dist.barrier()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        out = step()
-        evs[k][1].record(stream)
-        iters.append(out["iterations"])
-        rels.append(out["rel_kkt"])
-    torch.cuda.synchronize()
+    step_ms, iters, rels = timed(args.steps)
     dist.barrier()
     torch.cuda.synchronize()
     w1 = time.perf_counter()
     clk = clocks.stop()
     launches = prob.stats()["launches_total"] - launches0
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     dev_ms = sum(step_ms)
     tot_iters = sum(iters)
     all_iters = dist.reduce(tot_iters, "sum")
@@ -372,7 +405,7 @@ def run_ours(args, dist):
     # ---- roofline of the dominant kernel (NBJM sweep): per-launch events on
     # the solve stream, over the same K steps run again with timing on
     prob.set_option(lq2d.OPT_TIMING, 1)
-    sweep_ms, sweep_launches, delta_ms, delta_launches, fl_total, it_r = 0.0, 0, 0.0, 0, 0, 0
+    sweep_ms, sweep_launches, delta_ms, delta_launches, fl_total, by_total = 0.0, 0, 0.0, 0, 0, 0
     fl = sweep_flops(g)
     for _ in range(args.steps):
         flush.zero_()
@@ -383,20 +416,49 @@ def run_ours(args, dist):
         delta_ms += st["delta_ms"]
         delta_launches += st["delta_launches"]
         fl_total += sweep_flops_of_solve(fl, out["iterations"])
-        it_r += out["iterations"]
+        by_total += sweep_bytes_of_solve(g, out["iterations"])
     prob.set_option(lq2d.OPT_TIMING, 0)
-    achieved = fl_total / (sweep_ms / 1e3) / 1e12
-    roofline = {
-        "kernel": "nbjm_sweep_kernel<4,*>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-        "traffic": profiled_traffic(args.workload),
-        "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
-        "flops_per_launch": fl_total / max(sweep_launches, 1),
-        "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-        "measured": "CUDA events around each sweep launch on the solve stream, second pass over the same %d steps"
-                    % args.steps,
-        "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
-    }
+    measured_note = ("CUDA events around each sweep launch on the solve stream, second pass over the same %d steps"
+                     % args.steps)
+    if args.precision == "fp64":
+        achieved = fl_total / (sweep_ms / 1e3) / 1e12
+        roofline = {
+            "kernel": "nbjm_sweep_kernel<4,*,double>", "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": profiled_traffic(args.workload),
+            "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
+            "flops_per_launch": fl_total / max(sweep_launches, 1),
+            "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+            "measured": measured_note,
+            "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
+        }
+    else:
+        peak = measured_hbm_gbs()
+        achieved = by_total / (sweep_ms / 1e3) / 1e9
+        roofline = {
+            "kernel": "nbjm_sweep_kernel<4,*,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
+            "bytes_per_launch": by_total / max(sweep_launches, 1),
+            "fp32_tflops": fl_total / (sweep_ms / 1e3) / 1e12,
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "measured": measured_note,
+            "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
+        }
+
+    # ---- the same workload in the other precision, same protocol (FP64 plain vs mixed)
+    compare = None
+    if not args.no_compare and args.precision == "fp64":
+        prob.set_precision(1)
+        for _ in range(args.warmup):
+            step()
+        c_ms, c_its, c_rels = timed(args.steps)
+        prob.set_precision(0)
+        c_dev = sum(c_ms)
+        compare = {"precision": "mixed (FP32 preconditioner, FP64 residual/dots/updates)",
+                   "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT, "ms_per_step": c_dev / args.steps,
+                   "iterations_per_solve": sum(c_its) / len(c_its), "rel_kkt_residual": max(c_rels),
+                   "speedup_time_to_solve": dev_ms / c_dev}
 
     # ---- end to end: host (pinned) inputs in, host outputs back, per step
     xh = np.empty((g.T + 1, g.nodes, g.n))
@@ -426,9 +488,10 @@ def run_ours(args, dist):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
             "config": {"workload": args.workload, "K": g.K, "N": g.N, "T": g.T, "n": g.n, "m": g.m, "S": 2,
-                       "L": 2, "tol": args.tol, "precision": "fp64", "driver": args.driver,
+                       "L": 2, "tol": args.tol, "precision": args.precision, "driver": args.driver,
                        "l2": "flushed before each step (256 MiB write, outside the step events)",
                        "parallelism": "replicas" if dist.world > 1 else "single"},
             "time_to_solve_ms": dev_ms / args.steps,
@@ -436,6 +499,7 @@ def run_ours(args, dist):
             "rel_kkt_residual": max(rels),
             "wall_ms": (w1 - w0) * 1e3,
             "roofline": roofline,
+            "compare_mixed": compare,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk,

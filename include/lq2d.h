@@ -184,7 +184,15 @@ int lq2d_apply_delta_static(int K, int N, int T, int n, int m,
 int lq2d_set_option(lq2d_problem *h, int option, double value);
 int lq2d_get_stats(const lq2d_problem *h, lq2d_stats *out);
 
-/* 0 = FP64 everywhere (default). */
+/* Precision of the preconditioner (Algorithm 2).
+ *   0: FP64 everywhere (default).
+ *   1: the sweeps, the banded factors of Phi_bar and the Omega~/Xi~ blocks in
+ *      FP32; the residual, iterate, direction, Delta d, every dot product and
+ *      the stop test stay FP64.  The FP32 preconditioner is not exactly
+ *      symmetric, so the next direction uses the flexible ratio
+ *      q_new'(r_new - r_old) / mu_old.  The tolerance still applies to the
+ *      FP64 residual.  Mode 1 allocates FP32 copies of the operands on its
+ *      first use and refreshes them at every setup. */
 int lq2d_set_precision(lq2d_problem *h, int mode);
 
 /* Frees every device buffer of the handle; NULL is a no-op. */

@@ -10,24 +10,42 @@ namespace lq2d {
 constexpr int kOpThreads = 256;     // threads per block of the node-time kernels
 constexpr int kSweepThreads = 128;  // threads per block of the sweep kernels
 
+// Operands of the preconditioner in the precision VT of the sweeps (double,
+// or float in the mixed mode): the banded block-Cholesky factors of
+// Phi_bar, the Omega~ and Xi~ node blocks, and Q for the t = 0 blocks.
+template <typename VT>
+struct PrecData {
+  const VT* fac;
+  long long fac_rec;  // elements per pair-row record (24 n^2)
+  long long fac_vc;   // elements per (v, class) factor
+  const VT* Om;       // [NN][5][n][n]
+  const VT* AQ;       // [NN][5][n][n]
+  const VT* QAt;      // [NN][5][n][n]
+  const VT* Qm;       // [NN][n][n]
+};
+
 // Arguments of one NBJM sweep: theta_out = Phi~^-1 tau with
 //   tau = src                           (first sweep of the first outer step)
 //   tau = r + Xi~ delta_s               (first sweep of a later outer step; tau is kept in rtheta_out)
 //   tau = src + Omega~ theta_in         (later sweeps)
 // and, in the first sweep of a PCG step, the update of Algorithm 1 lines
 // 9-10 fused in front (delta += vartheta d, r -= vartheta y; tau = r).
-struct SweepArgs {
+// The iterates theta and delta_s are in the sweep precision VT; the PCG
+// vectors r, delta, y, d and the stored r_theta are always double.
+template <typename VT>
+struct SweepArgsT {
   const double* src;
   double* rtheta_out;
-  const double* delta_s;
-  const double* theta_in;
-  double* theta_out;
+  const VT* delta_s;
+  const VT* theta_in;
+  VT* theta_out;
   double* r;
   double* delta;
   const double* y;
   const double* d;
   double* partials;
 };
+using SweepArgs = SweepArgsT<double>;
 
 enum SweepVariant {
   kSweepPlain = 0,      // tau = src
@@ -38,15 +56,25 @@ enum SweepVariant {
 };
 
 struct KernelTable {
-  // z = Q~^-1 A~' dn with dn = q + beta d_old (beta from the state when use_beta)
+  // z = Q~^-1 A~' dn with dn = q + beta d_old (beta from the state when use_beta);
+  // q is the preconditioner output, double (FP64 mode) or float (mixed mode)
   void (*delta_z)(const Grid& g, const NodeData& nd, const double* q, const double* dold, double* z,
                   const SolverState* st, int use_beta, cudaStream_t s);
+  void (*delta_z_f32)(const Grid& g, const NodeData& nd, const float* q, const double* dold, double* z,
+                      const SolverState* st, int use_beta, cudaStream_t s);
   // y = A~ z + B~ R~^-1 B~' dn; in loop mode also writes dn into dout, reduces
   // y' dn and sets vartheta = mu / (y' dn) (Algorithm 1 lines 7-8)
   void (*delta_y)(const Grid& g, const NodeData& nd, const double* z, const double* q, const double* dold,
                   double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s);
-  void (*sweep)(int variant, const Grid& g, const NodeData& nd, const SweepArgs& a, SolverState* st,
-                cudaStream_t s);
+  void (*delta_y_f32)(const Grid& g, const NodeData& nd, const double* z, const float* q, const double* dold,
+                      double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s);
+  // FP64 sweep (Algorithm 2 step); the OmegaMu variant sets beta = mu_new / mu_old
+  void (*sweep)(int variant, const Grid& g, const PrecData<double>& pd, const SweepArgsT<double>& a,
+                SolverState* st, cudaStream_t s);
+  // FP32 sweep of the mixed mode; the OmegaMu variant sets the flexible
+  // beta = q_new'(r_new - r_old) / mu_old = -vartheta q_new'y / mu_old
+  void (*sweep_f32)(int variant, const Grid& g, const PrecData<float>& pd, const SweepArgsT<float>& a,
+                    SolverState* st, cudaStream_t s);
   // KKT residual pieces and cost of (x, u, delta): out[0] = sum of squared
   // residual entries, out[1] = x'Q~x + u'R~u, out[2] = max |A~x + B~u + omega~|
   void (*kkt)(const Grid& g, const NodeData& nd, const double* x, const double* u, const double* delta,
@@ -69,5 +97,7 @@ void launch_to_api(const double* intl, double* api, int NN, int slices, int comp
                    cudaStream_t s);
 void launch_recover_u(const Grid& g, const NodeData& nd, const double* delta, double* u, cudaStream_t s);
 void launch_loop_ctrl(SolverState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_to_f32(const double* src, float* dst, long long count, cudaStream_t s);
+void launch_to_f64(const float* src, double* dst, long long count, cudaStream_t s);
 
 }  // namespace lq2d

@@ -31,8 +31,8 @@ __device__ __forceinline__ const double* ahat_col(const NodeData& nd, int r, int
 // dn = q + beta d_old is formed on the fly (Algorithm 1 line 14 fused into
 // line 7); beta comes from the device state.
 // ---------------------------------------------------------------------------
-template <int NS>
-__global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd, const double* __restrict__ q,
+template <int NS, typename QT>
+__global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd, const QT* __restrict__ q,
                                                              const double* __restrict__ dold,
                                                              double* __restrict__ z,
                                                              const SolverState* __restrict__ st, int use_beta) {
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd
   double w[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    double dv = q[k * g.Ps + idx];
+    double dv = (double)q[k * g.Ps + idx];
     if (mix) dv += beta * dold[k * g.Ps + idx];
     w[k] = -dv;
   }
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd
       double dv[NS];
 #pragma unroll
       for (int c = 0; c < NS; ++c) {
-        dv[c] = q[c * g.Ps + ridx];
+        dv[c] = (double)q[c * g.Ps + ridx];
         if (mix) dv[c] += beta * dold[c * g.Ps + ridx];
       }
 #pragma unroll
@@ -86,9 +86,9 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd
 // Loop mode (Algorithm 1 lines 7-8, 14): dn = q + beta d_old is written back
 // to d (each thread owns its entry), y' dn is reduced and vartheta set.
 // ---------------------------------------------------------------------------
-template <int NS, bool LOOP>
+template <int NS, bool LOOP, typename QT>
 __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd, const double* __restrict__ z,
-                                                             const double* __restrict__ q,
+                                                             const QT* __restrict__ q,
                                                              const double* __restrict__ dold,
                                                              double* __restrict__ dout, double* __restrict__ y,
                                                              double* __restrict__ partials, SolverState* st) {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd
     double dn[NS], yk[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      double dv = q[k * g.Ps + idx];
+      double dv = (double)q[k * g.Ps + idx];
       if (LOOP && beta != 0.0) dv += beta * dold[k * g.Ps + idx];
       dn[k] = dv;
       yk[k] = -z[k * g.Ps + idx];
@@ -168,8 +168,12 @@ struct SweepGeom {
   static constexpr int BS = G2 * G2;
 };
 
-template <int NS, int VAR>
-__global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeData nd, SweepArgs a, SolverState* st) {
+template <int NS, int VAR, typename VT>
+__global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
+                                                                   SolverState* st) {
+  // VT = float is the mixed mode: FP32 factors, blocks and iterates, with
+  // the flexible (Polak-Ribiere) ratio for the next direction
+  constexpr bool FLEX = sizeof(VT) == 4;
   constexpr bool UPDATE = VAR == kSweepUpdate;
   constexpr bool XI = VAR == kSweepXi;
   constexpr bool OMEGA = VAR == kSweepOmega || VAR == kSweepOmegaMu;
@@ -190,28 +194,29 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeD
   const bool node_ok = active && al < G2 && j < g.N;
   const long long kP = (long long)k * g.Ps;
   const double vth = UPDATE ? st->theta : 0.0;
+  const bool flex_dot = FLEX && MU && st->have_mu;  // q'y is needed only after the first step
   double acc0 = 0.0, acc1 = 0.0;
 
   if (active) {
     const int cls = (t == g.T) ? 1 : 0;
-    const double* fac = nd.fac + (size_t)(2 * v + cls) * nd.fac_vc;
-    double ym1[G2], ym2[G2];
+    const VT* fac = pd.fac + (size_t)(2 * v + cls) * pd.fac_vc;
+    VT ym1[G2], ym2[G2];
 #pragma unroll
-    for (int b = 0; b < G2; ++b) { ym1[b] = 0.0; ym2[b] = 0.0; }
+    for (int b = 0; b < G2; ++b) { ym1[b] = VT(0); ym2[b] = VT(0); }
     for (int i = 0; i < g.K; ++i) {
       const int p = i * g.N + j;
       const long long off = node_ok ? (long long)p * Tp + t : 0;
-      double tau = 0.0;
+      VT tau = VT(0);
       if (node_ok) {
         if (UPDATE) {
           const double rr = a.r[kP + off] - vth * a.y[kP + off];
           a.r[kP + off] = rr;
           a.delta[kP + off] += vth * a.d[kP + off];
-          tau = rr;
+          tau = (VT)rr;
           acc0 += rr * rr;
           acc1 = fmax(acc1, fabs(rr));
         } else {
-          tau = a.src[kP + off];
+          tau = (VT)a.src[kP + off];
         }
         if (XI) {
           // (Xi~ delta)_t = A_hat Q^-1 delta_{t-1} + Q^-1 A_hat' delta_{t+1}
@@ -221,24 +226,24 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeD
             if (r < 0) continue;
             const long long rb = (long long)r * Tp + t;
             if (t >= 1) {
-              const double* blk = nd.AQ + (((size_t)p * 5 + dir) * NS + k) * NS;
+              const VT* blk = pd.AQ + (((size_t)p * 5 + dir) * NS + k) * NS;
 #pragma unroll
               for (int c = 0; c < NS; ++c) tau += blk[c] * a.delta_s[c * g.Ps + rb - 1];
             }
             if (t < g.T) {
-              const double* blk = nd.QAt + (((size_t)p * 5 + dir) * NS + k) * NS;
+              const VT* blk = pd.QAt + (((size_t)p * 5 + dir) * NS + k) * NS;
 #pragma unroll
               for (int c = 0; c < NS; ++c) tau += blk[c] * a.delta_s[c * g.Ps + rb + 1];
             }
           }
-          a.rtheta_out[kP + off] = tau;
+          a.rtheta_out[kP + off] = (double)tau;
         }
         if (OMEGA && t >= 1) {
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
             const int qn = offpair_node(i, j, o, g.K, g.N);
             if (qn < 0) continue;
-            const double* blk = nd.Om + (((size_t)p * 5 + o) * NS + k) * NS;
+            const VT* blk = pd.Om + (((size_t)p * 5 + o) * NS + k) * NS;
             const long long qb = (long long)qn * Tp + t;
 #pragma unroll
             for (int c = 0; c < NS; ++c) tau += blk[c] * a.theta_in[c * g.Ps + qb];
@@ -247,22 +252,23 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeD
       }
       if (t == 0) {
         // Phi_bar_{v,0} = blkdiag(Q^-1): theta = Q tau, node by node
-        double out = 0.0;
-        const double* Qrow = nd.Qm + ((size_t)p * NS + k) * NS;
+        VT out = VT(0);
+        const VT* Qrow = pd.Qm + ((size_t)p * NS + k) * NS;
 #pragma unroll
         for (int c = 0; c < NS; ++c) {
-          const double tc = __shfl_sync(gmask, tau, jj * NS + c, GS);
+          const VT tc = __shfl_sync(gmask, tau, jj * NS + c, GS);
           if (node_ok) out += Qrow[c] * tc;
         }
         if (node_ok) {
           a.theta_out[kP + off] = out;
-          if (MU) acc0 += out * a.r[kP + off];
+          if (MU) acc0 += (double)out * a.r[kP + off];
+          if (flex_dot) acc1 += (double)out * a.y[kP + off];
         }
         continue;
       }
       // forward substitution over pair-row i
-      const double* rec = fac + (size_t)i * nd.fac_rec;
-      double w = tau;
+      const VT* rec = fac + (size_t)i * pd.fac_rec;
+      VT w = tau;
       if (i >= 1) {
 #pragma unroll
         for (int b = 0; b < G2; ++b) w -= rec[BS + b * G2 + ac] * ym1[b];
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeD
 #pragma unroll
         for (int b = 0; b < G2; ++b) w -= rec[b * G2 + ac] * ym2[b];
       }
-      double yv = 0.0;
+      VT yv = VT(0);
 #pragma unroll
       for (int b = 0; b < G2; ++b) yv += rec[2 * BS + b * G2 + ac] * __shfl_sync(gmask, w, b, GS);
       if (node_ok) a.theta_out[kP + off] = yv;
@@ -282,30 +288,31 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeD
       }
     }
     if (t >= 1) {
-      double xp1[G2], xp2[G2];
+      VT xp1[G2], xp2[G2];
 #pragma unroll
-      for (int b = 0; b < G2; ++b) { xp1[b] = 0.0; xp2[b] = 0.0; }
+      for (int b = 0; b < G2; ++b) { xp1[b] = VT(0); xp2[b] = VT(0); }
       for (int i = g.K - 1; i >= 0; --i) {
         const int p = i * g.N + j;
         const long long off = node_ok ? (long long)p * Tp + t : 0;
-        const double* rec = fac + (size_t)i * nd.fac_rec;
-        double w = node_ok ? a.theta_out[kP + off] : 0.0;
+        const VT* rec = fac + (size_t)i * pd.fac_rec;
+        VT w = node_ok ? a.theta_out[kP + off] : VT(0);
         if (i + 1 < g.K) {
-          const double* r1 = rec + nd.fac_rec;
+          const VT* r1 = rec + pd.fac_rec;
 #pragma unroll
           for (int b = 0; b < G2; ++b) w -= r1[4 * BS + b * G2 + ac] * xp1[b];
         }
         if (i + 2 < g.K) {
-          const double* r2 = rec + 2 * nd.fac_rec;
+          const VT* r2 = rec + 2 * pd.fac_rec;
 #pragma unroll
           for (int b = 0; b < G2; ++b) w -= r2[3 * BS + b * G2 + ac] * xp2[b];
         }
-        double xv = 0.0;
+        VT xv = VT(0);
 #pragma unroll
         for (int b = 0; b < G2; ++b) xv += rec[5 * BS + b * G2 + ac] * __shfl_sync(gmask, w, b, GS);
         if (node_ok) {
           a.theta_out[kP + off] = xv;
-          if (MU) acc0 += xv * a.r[kP + off];
+          if (MU) acc0 += (double)xv * a.r[kP + off];
+          if (flex_dot) acc1 += (double)xv * a.y[kP + off];
         }
 #pragma unroll
         for (int b = 0; b < G2; ++b) {
@@ -331,12 +338,15 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, NodeD
   }
   if (MU) {
     double tot0, tot1;
-    if (grid_reduce2<false>(acc0, 0.0, a.partials, &st->counters[kCntMu], &tot0, &tot1)) {
-      // Algorithm 1 lines 13-14: mu^(i+1) and the ratio used for d^(i+1)
-      if (!(tot0 > 0.0) || !isfinite(tot0)) {
+    if (grid_reduce2<false>(acc0, acc1, a.partials, &st->counters[kCntMu], &tot0, &tot1)) {
+      // Algorithm 1 lines 13-14: mu^(i+1) and the ratio used for d^(i+1);
+      // the mixed mode takes q^(i+1)'(r^(i+1) - r^(i)) / mu^(i), which equals
+      // mu^(i+1) / mu^(i) for an exactly symmetric preconditioner
+      if (!(tot0 > 0.0) || !isfinite(tot0) || !isfinite(tot1)) {
         st->done = kBreakdown;
       } else {
-        st->beta = st->have_mu ? tot0 / st->mu : 0.0;
+        if (!st->have_mu) st->beta = 0.0;
+        else st->beta = FLEX ? (-st->theta * tot1) / st->mu : tot0 / st->mu;
         st->mu = tot0;
         st->have_mu = 1;
       }
@@ -441,35 +451,37 @@ __global__ void __launch_bounds__(kOpThreads) kkt_kernel(Grid g, NodeData nd, co
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int NS>
-void launch_delta_z(const Grid& g, const NodeData& nd, const double* q, const double* dold, double* z,
+template <int NS, typename QT>
+void launch_delta_z(const Grid& g, const NodeData& nd, const QT* q, const double* dold, double* z,
                     const SolverState* st, int use_beta, cudaStream_t s) {
   const long long blocks = (g.P + kOpThreads - 1) / kOpThreads;
-  delta_z_kernel<NS><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, q, dold, z, st, use_beta);
+  delta_z_kernel<NS, QT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, q, dold, z, st, use_beta);
 }
 
-template <int NS>
-void launch_delta_y(const Grid& g, const NodeData& nd, const double* z, const double* q, const double* dold,
+template <int NS, typename QT>
+void launch_delta_y(const Grid& g, const NodeData& nd, const double* z, const QT* q, const double* dold,
                     double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s) {
   const long long blocks = (g.P + kOpThreads - 1) / kOpThreads;
   if (loop_mode)
-    delta_y_kernel<NS, true><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, z, q, dold, dout, y, partials, st);
+    delta_y_kernel<NS, true, QT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, z, q, dold, dout, y, partials, st);
   else
-    delta_y_kernel<NS, false><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, z, q, dold, dout, y, partials, st);
+    delta_y_kernel<NS, false, QT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, z, q, dold, dout, y, partials, st);
 }
 
-template <int NS>
-void launch_sweep(int variant, const Grid& g, const NodeData& nd, const SweepArgs& a, SolverState* st,
+template <int NS, typename VT>
+void launch_sweep(int variant, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a, SolverState* st,
                   cudaStream_t s) {
   constexpr int GS = SweepGeom<NS>::GS;
   const long long threads = (long long)g.V * (g.T + 1) * GS;
   const unsigned blocks = (unsigned)((threads + kSweepThreads - 1) / kSweepThreads);
   switch (variant) {
-    case kSweepPlain: nbjm_sweep_kernel<NS, kSweepPlain><<<blocks, kSweepThreads, 0, s>>>(g, nd, a, st); break;
-    case kSweepUpdate: nbjm_sweep_kernel<NS, kSweepUpdate><<<blocks, kSweepThreads, 0, s>>>(g, nd, a, st); break;
-    case kSweepOmega: nbjm_sweep_kernel<NS, kSweepOmega><<<blocks, kSweepThreads, 0, s>>>(g, nd, a, st); break;
-    case kSweepOmegaMu: nbjm_sweep_kernel<NS, kSweepOmegaMu><<<blocks, kSweepThreads, 0, s>>>(g, nd, a, st); break;
-    default: nbjm_sweep_kernel<NS, kSweepXi><<<blocks, kSweepThreads, 0, s>>>(g, nd, a, st); break;
+    case kSweepPlain: nbjm_sweep_kernel<NS, kSweepPlain, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
+    case kSweepUpdate: nbjm_sweep_kernel<NS, kSweepUpdate, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
+    case kSweepOmega: nbjm_sweep_kernel<NS, kSweepOmega, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
+    case kSweepOmegaMu:
+      nbjm_sweep_kernel<NS, kSweepOmegaMu, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st);
+      break;
+    default: nbjm_sweep_kernel<NS, kSweepXi, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
   }
 }
 
@@ -482,7 +494,10 @@ void launch_kkt(const Grid& g, const NodeData& nd, const double* x, const double
 
 template <int NS>
 const KernelTable* make_table() {
-  static const KernelTable t = {&launch_delta_z<NS>, &launch_delta_y<NS>, &launch_sweep<NS>, &launch_kkt<NS>};
+  static const KernelTable t = {&launch_delta_z<NS, double>, &launch_delta_z<NS, float>,
+                                &launch_delta_y<NS, double>, &launch_delta_y<NS, float>,
+                                &launch_sweep<NS, double>,   &launch_sweep<NS, float>,
+                                &launch_kkt<NS>};
   return &t;
 }
 

@@ -159,6 +159,16 @@ __global__ void loop_ctrl_kernel(SolverState* st, cudaGraphConditionalHandle h) 
   cudaGraphSetConditional(h, keep ? 1u : 0u);
 }
 
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (float)src[i];
+}
+
+__global__ void to_f64_kernel(const float* __restrict__ src, double* __restrict__ dst, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (double)src[i];
+}
+
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -200,6 +210,14 @@ void launch_recover_u(const Grid& g, const NodeData& nd, const double* delta, do
 
 void launch_loop_ctrl(SolverState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
   loop_ctrl_kernel<<<1, 1, 0, s>>>(st, h);
+}
+
+void launch_to_f32(const double* src, float* dst, long long count, cudaStream_t s) {
+  to_f32_kernel<<<blocks_for(count, 256), 256, 0, s>>>(src, dst, count);
+}
+
+void launch_to_f64(const float* src, double* dst, long long count, cudaStream_t s) {
+  to_f64_kernel<<<blocks_for(count, 256), 256, 0, s>>>(src, dst, count);
 }
 
 }  // namespace lq2d

@@ -30,7 +30,7 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 struct GraphEntry {
-  int S = 0, L = 0;
+  int S = 0, L = 0, precision = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -75,6 +75,11 @@ struct lq2d_problem {
   lq2d_stats stats{};
   std::vector<cudaEvent_t> ev_pool;
   long long launches = 0;  // kernels launched on behalf of this handle since creation
+  // precision of the preconditioner: 0 = FP64, 1 = FP32 sweeps and factors
+  int precision = 0;
+  PrecData<double> pd64{};
+  PrecData<float> pd32{};
+  float* f32_buf = nullptr;  // FP32 copies of the factors and node blocks (mode 1, allocated on first use)
   int graph_body_kernels = 0;  // kernels per device-loop body of the last graph launch (0: no graph)
 };
 
@@ -189,7 +194,32 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   nd.Aself = sb.Aself; nd.Anb = sb.Anb; nd.Bm = sb.Bm; nd.Qm = sb.Qm; nd.QTm = sb.QTm; nd.Rm = sb.Rm;
   nd.Qi = sb.Qi; nd.QTi = sb.QTi; nd.Sb = sb.Sb; nd.RiBt = sb.RiBt; nd.Om = sb.Om; nd.AQ = sb.AQ;
   nd.QAt = sb.QAt; nd.fac = sb.fac; nd.fac_rec = fac_rec; nd.fac_vc = fac_vc;
+  h->pd64 = PrecData<double>{sb.fac, fac_rec, fac_vc, sb.Om, sb.AQ, sb.QAt, sb.Qm};
   return LQ2D_OK;
+}
+
+// Element counts of the preconditioner operands: factors, Omega~, AQ, QAt, Q.
+void prec_counts(const lq2d_problem* h, long long c[5]) {
+  const Grid& g = h->g;
+  const long long nn = (long long)g.n * g.n;
+  c[0] = (long long)g.V * 2 * h->nd.fac_vc;
+  c[1] = (long long)g.NN * 5 * nn;
+  c[2] = c[1];
+  c[3] = c[1];
+  c[4] = (long long)g.NN * nn;
+}
+
+// FP32 copies of the preconditioner operands for the mixed mode.
+void convert_prec_f32(lq2d_problem* h, cudaStream_t s) {
+  long long c[5];
+  prec_counts(h, c);
+  const double* src[5] = {h->sb.fac, h->sb.Om, h->sb.AQ, h->sb.QAt, h->sb.Qm};
+  float* dst = h->f32_buf;
+  for (int a = 0; a < 5; ++a) {
+    launch_to_f32(src[a], dst, c[a], s);
+    dst += c[a];
+  }
+  h->launches += 5;
 }
 
 // Setup on `s`: inverses, splitting blocks, factors, right-hand side and its
@@ -198,6 +228,7 @@ int run_setup(lq2d_problem* h, cudaStream_t s) {
   const Grid& g = h->g;
   LQ_CUDA(cudaMemsetAsync(h->setup_status, 0, sizeof(int), s));
   launch_setup(h->sb, g.K, g.N, g.n, g.m, g.V, h->nd.fac_rec, h->nd.fac_vc, h->setup_status, s);
+  if (h->f32_buf) convert_prec_f32(h, s);
   launch_build_rhs(g, h->sb.x0, h->w_aff, h->rhs, s);
   launch_norms(g, h->rhs, g.n, h->partials, &h->st->counters[kCntAux], h->bnorm, s);
   h->launches += 7;
@@ -247,24 +278,26 @@ int create_common(lq2d_problem** out, int K, int N, int T, int n, int m, const d
 // One preconditioner application q = D_S r_in (Algorithm 2, S x L sweeps
 // from zero starts).  fuse_update: the first sweep also performs Algorithm 1
 // lines 9-11; mu: the last sweep reduces mu = q' r.  Returns the buffer
-// holding q (thB, since S*L is even).
-const double* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
+// holding q (thB, since S*L is even); its elements are double in FP64 mode
+// and float in the mixed mode.
+template <typename VT>
+const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
                               const double* r_in, cudaStream_t s, bool timing) {
-  double* bufs[2] = {h->thA, h->thB};
+  VT* bufs[2] = {reinterpret_cast<VT*>(h->thA), reinterpret_cast<VT*>(h->thB)};
   int out_i = 0;
-  const double* prev = nullptr;
+  const VT* prev = nullptr;
   for (int so = 0; so < S; ++so) {
     for (int l = 0; l < L; ++l) {
-      SweepArgs a{};
+      SweepArgsT<VT> a{};
       a.partials = h->partials;
       a.theta_out = bufs[out_i];
+      a.y = h->y;
       int variant;
       if (l == 0 && so == 0) {
         variant = fuse_update ? kSweepUpdate : kSweepPlain;
         a.src = r_in;
         a.r = const_cast<double*>(r_in);
         a.delta = h->delta;
-        a.y = h->y;
         a.d = h->d;
       } else if (l == 0) {
         variant = kSweepXi;
@@ -287,7 +320,10 @@ const double* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, b
         e1 = h->ev_pool[k + 1];
         cudaEventRecord(e0, s);
       }
-      h->kt->sweep(variant, h->g, h->nd, a, st, s);
+      if constexpr (sizeof(VT) == 4)
+        h->kt->sweep_f32(variant, h->g, h->pd32, a, st, s);
+      else
+        h->kt->sweep(variant, h->g, h->pd64, a, st, s);
       h->launches += 1;
       if (timing) cudaEventRecord(e1, s);
       prev = bufs[out_i];
@@ -297,7 +333,15 @@ const double* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, b
   return prev;
 }
 
-void enqueue_delta(lq2d_problem* h, const double* q, const double* dold, double* dout, double* y,
+const void* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
+                            const double* r_in, cudaStream_t s, bool timing) {
+  if (h->precision == 1) return enqueue_precond_t<float>(h, S, L, fuse_update, mu, st, r_in, s, timing);
+  return enqueue_precond_t<double>(h, S, L, fuse_update, mu, st, r_in, s, timing);
+}
+
+// y = Delta dn with dn = q + beta d_old; q is the preconditioner output in
+// the preconditioner's precision.
+void enqueue_delta(lq2d_problem* h, const void* q, const double* dold, double* dout, double* y,
                    SolverState* st, bool loop, cudaStream_t s, bool timing) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (timing) {
@@ -310,8 +354,15 @@ void enqueue_delta(lq2d_problem* h, const double* q, const double* dold, double*
     e1 = h->ev_pool[k + 1];
     cudaEventRecord(e0, s);
   }
-  h->kt->delta_z(h->g, h->nd, q, dold, h->z, st, loop ? 1 : 0, s);
-  h->kt->delta_y(h->g, h->nd, h->z, q, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+  if (h->precision == 1) {
+    const float* qf = static_cast<const float*>(q);
+    h->kt->delta_z_f32(h->g, h->nd, qf, dold, h->z, st, loop ? 1 : 0, s);
+    h->kt->delta_y_f32(h->g, h->nd, h->z, qf, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+  } else {
+    const double* qd = static_cast<const double*>(q);
+    h->kt->delta_z(h->g, h->nd, qd, dold, h->z, st, loop ? 1 : 0, s);
+    h->kt->delta_y(h->g, h->nd, h->z, qd, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+  }
   h->launches += 2;
   if (timing) cudaEventRecord(e1, s);
 }
@@ -326,7 +377,7 @@ void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
 
 int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   for (int i = 0; i < h->ngraphs; ++i)
-    if (h->graphs[i].S == S && h->graphs[i].L == L) {
+    if (h->graphs[i].S == S && h->graphs[i].L == L && h->graphs[i].precision == h->precision) {
       *exec = h->graphs[i].exec;
       return LQ2D_OK;
     }
@@ -339,6 +390,7 @@ int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   GraphEntry ge;
   ge.S = S;
   ge.L = L;
+  ge.precision = h->precision;
   LQ_CUDA(cudaGraphCreate(&ge.graph, 0));
   cudaGraphConditionalHandle hc;
   LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, ge.graph, 1u, cudaGraphCondAssignDefault));
@@ -678,8 +730,15 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
   const Grid& g = h->g;
   h->launches += 2;
   launch_to_internal(static_cast<const double*>(d_r), h->y, g.NN, g.T + 1, g.n, g.Ps, s);
-  const double* q = enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
-  launch_to_api(q, static_cast<double*>(d_q), g.NN, g.T + 1, g.n, g.Ps, s);
+  const void* q = enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
+  const double* qd = static_cast<const double*>(q);
+  if (h->precision == 1) {
+    // widen the FP32 result into thA (free after the sweeps) before the layout change
+    launch_to_f64(static_cast<const float*>(q), h->thA, (long long)g.Ps * g.n, s);
+    h->launches += 1;
+    qd = h->thA;
+  }
+  launch_to_api(qd, static_cast<double*>(d_q), g.NN, g.T + 1, g.n, g.Ps, s);
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
   return LQ2D_OK;
@@ -718,7 +777,32 @@ int lq2d_get_stats(const lq2d_problem* h, lq2d_stats* out) {
 
 int lq2d_set_precision(lq2d_problem* h, int mode) {
   if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
-  if (mode != 0) return fail(LQ2D_EINVAL, "unknown precision mode");
+  if (mode != 0 && mode != 1) return fail(LQ2D_EINVAL, "precision mode must be 0 (FP64) or 1 (FP32 preconditioner)");
+  if (mode == 1 && !h->f32_buf) {
+    long long c[5];
+    prec_counts(h, c);
+    const long long total = c[0] + c[1] + c[2] + c[3] + c[4];
+    double* buf = nullptr;
+    int rc = dev_alloc(h, &buf, (size_t)(total + 1) / 2 + 64);
+    if (rc) return rc;
+    h->f32_buf = reinterpret_cast<float*>(buf);
+    float* p = h->f32_buf;
+    h->pd32.fac = p;
+    p += c[0];
+    h->pd32.Om = p;
+    p += c[1];
+    h->pd32.AQ = p;
+    p += c[2];
+    h->pd32.QAt = p;
+    p += c[3];
+    h->pd32.Qm = p;
+    h->pd32.fac_rec = h->nd.fac_rec;
+    h->pd32.fac_vc = h->nd.fac_vc;
+    convert_prec_f32(h, nullptr);
+    LQ_CUDA(cudaStreamSynchronize(nullptr));
+    LQ_CUDA(cudaGetLastError());
+  }
+  h->precision = mode;
   return LQ2D_OK;
 }
 
