@@ -375,6 +375,53 @@ def nbjm_closed_form(Sp: Splitting, S: int, L: int) -> np.ndarray:
     return D
 
 
+@dataclasses.dataclass
+class NBJMResult:
+    delta: np.ndarray
+    outer_iterations: int
+    converged: bool
+
+
+def nbjm_solve(Sp: Splitting, r_delta: np.ndarray, L: int, eps: float, max_outer: int,
+               phi: Optional["PhiSolver"] = None, inner_start: str = "outer") -> NBJMResult:
+    """Algorithm 2 as a solver (the paper's "standard nested block Jacobi",
+    Section V): outer iterations with L inner sweeps each, until
+    ||delta^(s+1) - delta^(s)||_inf < eps (its exit line; reading A8 keeps
+    this exit out of the preconditioner).
+
+    inner_start="outer" (reading A22) starts every inner iteration from the
+    current outer iterate, theta^(0) = delta^(s), as the two-stage methods
+    the paper cites do; its fixed point solves Delta delta = r_delta.
+    inner_start="zero" is Algorithm 2 exactly as printed (theta^(0) = 0),
+    whose fixed point solves (Upsilon_L^-1 - Xi~) delta = r_delta instead."""
+    phi = phi if phi is not None else PhiSolver(Sp)
+    delta = np.zeros_like(r_delta)
+    for s in range(max_outer):
+        r_theta = r_delta + Sp.Xi @ delta
+        theta = delta.copy() if inner_start == "outer" else np.zeros_like(r_delta)
+        for _l in range(L):
+            theta = phi.solve(r_theta + Sp.Omega @ theta)
+        change = np.max(np.abs(theta - delta))
+        delta = theta
+        if change < eps:
+            return NBJMResult(delta, s + 1, True)
+    return NBJMResult(delta, max_outer, False)
+
+
+def lanczos_extremes(alphas, betas):
+    """Extreme eigenvalues of the Lanczos tridiagonal matrix built from the
+    CG coefficients (Saad, Iterative Methods, Section 6.7.3): diagonal
+    1/a_0, 1/a_j + b_{j-1}/a_{j-1}; off-diagonal sqrt(b_j)/a_j."""
+    a = np.asarray(alphas, dtype=np.float64)
+    b = np.asarray(betas, dtype=np.float64)
+    m = len(a)
+    diag = 1.0 / a
+    diag[1:] += b[: m - 1] / a[: m - 1]
+    off = np.sqrt(b[: m - 1]) / a[: m - 1]
+    ev = sla.eigvalsh_tridiagonal(diag, off)
+    return ev[0], ev[-1]
+
+
 # --------------------------------------------------------------------------
 # Algorithm 1 (PCGM)
 # --------------------------------------------------------------------------
@@ -386,6 +433,8 @@ class PCGResult:
     converged: bool
     residual_history: list
     restarts: int
+    alphas: list = dataclasses.field(default_factory=list)
+    betas: list = dataclasses.field(default_factory=list)
 
 
 def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray], np.ndarray],
@@ -405,21 +454,23 @@ def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray
 
     delta = np.zeros_like(r_delta) if delta0 is None else np.array(delta0, dtype=np.float64)
     hist = []
+    alphas, betas = [], []
     it = 0
     restarts = 0
     while True:
         r = r_delta - Delta @ delta                       # line 2
         hist.append(np.linalg.norm(r))
         if passed(r):                                     # reading A10
-            return PCGResult(delta, it, True, hist, restarts)
+            return PCGResult(delta, it, True, hist, restarts, alphas, betas)
         if it >= max_iter:
-            return PCGResult(delta, it, False, hist, restarts)
+            return PCGResult(delta, it, False, hist, restarts, alphas, betas)
         d = precond(r)                                    # line 3
         mu = d @ r                                        # line 4
         converged = False
         while it < max_iter:                              # line 6
             y = Delta @ d                                 # line 7
             theta = mu / (y @ d)                          # line 8
+            alphas.append(theta)
             delta = delta + theta * d                     # line 9
             r = r - theta * y                             # line 10
             it += 1
@@ -429,12 +480,13 @@ def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray
                 break
             q = precond(r)                                # line 12
             mu_new = q @ r                                # line 13
+            betas.append(mu_new / mu)
             d = q + (mu_new / mu) * d                     # line 14
             mu = mu_new
         if not converged:
-            return PCGResult(delta, it, False, hist, restarts)
+            return PCGResult(delta, it, False, hist, restarts, alphas, betas)
         if not confirm_true_residual or passed(r_delta - Delta @ delta):
-            return PCGResult(delta, it, True, hist, restarts)
+            return PCGResult(delta, it, True, hist, restarts, alphas, betas)
         restarts += 1
 
 

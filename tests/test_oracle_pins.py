@@ -347,3 +347,51 @@ def test_row_evaluation_matches_assembled_delta():
     got = O.delta_rows_matrix_free(P, rows, v)
     ref = orc.Delta @ v
     assert np.allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_standalone_nbjm_converges_to_the_kkt_solution():
+    """Algorithm 2 run to its exit test converges (Section IV: the splittings
+    are convergent) to the solution of Delta delta = r_delta, and needs far
+    more iterations than PCGM (Section V)."""
+    g = synth.random_grid(3, 4, 5, 2, 1, seed=91)
+    orc = O.Oracle(as_problem(g))
+    res = O.nbjm_solve(orc.splitting, orc.r_delta, 2, 1e-13, 200000, orc.phi)
+    assert res.converged
+    ref = orc.solve_direct().delta.ravel()
+    assert np.linalg.norm(res.delta - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert res.outer_iterations > orc.solve(1e-10).iterations
+
+
+def test_algorithm2_with_zero_inner_start_has_a_shifted_fixed_point():
+    """Reading A22: with theta^(0) = 0 at every outer step (Algorithm 2 as
+    printed), the outer iteration is delta <- Upsilon_L (r + Xi~ delta), whose
+    fixed point is (Upsilon_L^-1 - Xi~)^-1 r, not Delta^-1 r."""
+    g = synth.random_grid(3, 4, 5, 2, 1, seed=91)
+    orc = O.Oracle(as_problem(g))
+    Sp = orc.splitting
+    res = O.nbjm_solve(Sp, orc.r_delta, 2, 1e-13, 200000, orc.phi, inner_start="zero")
+    assert res.converged
+    U = O.upsilon_dense(Sp, 2)
+    fixed = np.linalg.solve(np.linalg.inv(U) - Sp.Xi.toarray(), orc.r_delta)
+    assert np.linalg.norm(res.delta - fixed) <= 1e-8 * np.linalg.norm(fixed)
+    exact = orc.solve_direct().delta.ravel()
+    assert np.linalg.norm(fixed - exact) > 1e-3 * np.linalg.norm(exact)
+
+
+def test_lanczos_estimates_match_dense_condition_numbers():
+    """The extreme Ritz values of the Lanczos matrix built from the PCG
+    coefficients bracket, and after enough steps match, the spectrum of the
+    preconditioned operator (Saad 6.7.3)."""
+    g = synth.workload("grid4_T20")
+    orc = O.Oracle(as_problem(g))
+    D = orc.Delta.toarray()
+    ev = np.linalg.eigvalsh(D)
+    cg = O.pcg(orc.Delta, orc.r_delta, lambda r: r, 1e-13, 100000)
+    lo, hi = O.lanczos_extremes(cg.alphas, cg.betas)
+    assert abs(hi / lo - ev[-1] / ev[0]) <= 0.02 * ev[-1] / ev[0]
+    assert lo >= ev[0] * (1 - 1e-8) and hi <= ev[-1] * (1 + 1e-8)
+    DS = O.nbjm_closed_form(orc.splitting, 2, 2)
+    evp = sla.eigh(D, np.linalg.inv(DS), eigvals_only=True)
+    pc = O.pcg(orc.Delta, orc.r_delta, orc.preconditioner(2, 2).apply, 1e-13, 10000)
+    lo, hi = O.lanczos_extremes(pc.alphas, pc.betas)
+    assert abs(hi / lo - evp[-1] / evp[0]) <= 0.02 * evp[-1] / evp[0]
