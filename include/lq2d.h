@@ -65,8 +65,14 @@ enum {
                                    few steps */
   LQ2D_OPT_TIMING = 3,       /* 1: record CUDA events around every sweep and Delta-apply launch
                                    (forces driver 1); read the totals with lq2d_get_stats */
-  LQ2D_OPT_MAX_RESTARTS = 4  /* restarts allowed when the recurrence residual passes but the
+  LQ2D_OPT_MAX_RESTARTS = 4, /* restarts allowed when the recurrence residual passes but the
                                 true residual does not (default 3) */
+  LQ2D_OPT_PRECONDITIONER = 5, /* 0: NBJM, Algorithm 2 (default); 1: none (plain CG on Delta,
+                                  used to estimate kappa(Delta)) */
+  LQ2D_OPT_KAPPA = 6          /* 1: record the PCG coefficients of each solve and estimate the
+                                  extreme eigenvalues of the preconditioned operator (Lanczos
+                                  matrix of CG; Section V reports kappa before and after
+                                  preconditioning); read them with lq2d_get_stats */
 };
 
 /* Statistics of the last solve on a handle. */
@@ -85,7 +91,10 @@ typedef struct lq2d_stats {
   double delta_ms;         /* summed device time of the timed Delta-apply launches */
   long long launches_total; /* kernels launched for this handle since creation (setup included) */
   int body_executions;     /* device-loop body executions in the last solve */
-  int pad2;
+  int outer_iterations;    /* outer steps of the last standalone NBJM solve */
+  double kappa_estimate;   /* lambda_max / lambda_min (LQ2D_OPT_KAPPA), else 0 */
+  double lambda_min;       /* extreme Ritz values of the preconditioned operator */
+  double lambda_max;
 } lq2d_stats;
 
 /* Creates a problem from host arrays, copies them to the current device and
@@ -147,6 +156,21 @@ int lq2d_solve(lq2d_problem *h, double tol, int outer_S, int inner_L, int max_it
 int lq2d_solve_device(lq2d_problem *h, double tol, int outer_S, int inner_L, int max_iter,
                       const void *d_delta0, void *d_x, void *d_u, void *d_costate,
                       int *iterations, double *rel_kkt_residual, void *stream);
+
+/* Algorithm 2 run as a solver: the "standard nested block Jacobi method" the
+ * paper compares PCGM against (Section V).  Each outer step runs inner_L
+ * sweeps (L = 2 in the paper) and stops when
+ * ||delta^(s+1) - delta^(s)||_inf < eps (the exit line of Algorithm 2).
+ * Each inner iteration starts from the current outer iterate, theta^(0) =
+ * delta^(s): with a zero inner start at every outer step, as printed, the
+ * fixed point would be (Upsilon_L^-1 - Xi~)^-1 r_delta instead of the
+ * solution.  Honours lq2d_set_precision.  Device buffers as in
+ * lq2d_solve_device; outer_iterations and rel_kkt_residual are optional
+ * outputs.  LQ2D_ENOCONV when max_outer steps do not pass the exit test
+ * (outputs still written). */
+int lq2d_solve_nbjm_device(lq2d_problem *h, double eps, int inner_L, int max_outer,
+                           void *d_x, void *d_u, void *d_costate,
+                           int *outer_iterations, double *rel_kkt_residual, void *stream);
 
 /* y = Delta d (Section II-B, the product of Algorithm 1 line 7), device
  * buffers [T+1][K*N][n].  Returns after the work on `stream` is complete. */

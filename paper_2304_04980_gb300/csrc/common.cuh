@@ -34,9 +34,19 @@ struct SolverState {
   int have_mu;        // 0 before the first preconditioner application
   int body_count;     // executions of the device-loop body
   int body_cap;       // hard cap on body executions
-  int pad0;
+  int hist_cap;       // entries (pairs) available in hist
   unsigned int counters[8];  // arrival counters of the last-block reductions
+  double* hist;       // optional: vartheta_j at [2j], beta_j at [2j+1] (Lanczos estimate), or NULL
 };
+
+// Records the PCG coefficients of step j (called by the last block of the
+// reductions that produce them).
+__device__ inline void record_theta(SolverState* st, int j) {
+  if (st->hist != nullptr && j >= 0 && j < st->hist_cap) st->hist[2 * j] = st->theta;
+}
+__device__ inline void record_beta(SolverState* st, int j) {
+  if (st->hist != nullptr && j >= 0 && j < st->hist_cap) st->hist[2 * j + 1] = st->beta;
+}
 
 enum StateDone { kRunning = 0, kConverged = 1, kMaxIter = 2, kBreakdown = 3, kLoopCap = 4 };
 enum CounterSlot { kCntDot = 0, kCntNorm = 1, kCntMu = 2, kCntInit = 3, kCntKkt = 4, kCntAux = 5 };

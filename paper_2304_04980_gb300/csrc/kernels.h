@@ -53,6 +53,8 @@ enum SweepVariant {
   kSweepOmega = 2,      // tau = src + Omega~ theta_in
   kSweepOmegaMu = 3,    // as kSweepOmega, plus mu = theta_out' r reduced (last sweep)
   kSweepXi = 4,         // tau = r + Xi~ delta_s, written to rtheta_out
+  kSweepXiOmega = 5,    // tau = r + Xi~ delta_s + Omega~ theta_in (theta_in = delta_s): the first inner
+                        // sweep of the standalone NBJM solver, started from the outer iterate
 };
 
 struct KernelTable {
@@ -79,13 +81,22 @@ struct KernelTable {
   // residual entries, out[1] = x'Q~x + u'R~u, out[2] = max |A~x + B~u + omega~|
   void (*kkt)(const Grid& g, const NodeData& nd, const double* x, const double* u, const double* delta,
               const double* rhs, double* partials, SolverState* st, double* out, cudaStream_t s);
+  // sets the sweep kernels' shared-memory limits on the current device
+  cudaError_t (*prepare)();
 };
 
 const KernelTable* kernel_table(int n);
 
 // dimension-generic helpers (kernels_misc.cu)
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
-                       int keep_iter, cudaStream_t s);
+                       int keep_iter, double* hist, int hist_cap, cudaStream_t s);
+// identity preconditioner (plain CG): q = r, mu = r'r; with update, the PCG
+// update of Algorithm 1 lines 9-11 first
+void launch_ident(const Grid& g, bool update, double* r, double* delta, const double* y, const double* d,
+                  double* q, double* partials, SolverState* st, cudaStream_t s);
+// standalone NBJM exit test: max |a - b| (b = NULL: max |a|) < eps, counts the outer step
+void launch_nbjm_diff(const Grid& g, const void* a, const void* b, int fp32, double* partials, SolverState* st,
+                      cudaStream_t s);
 void launch_init_residual(const Grid& g, const double* rhs, const double* y, double* r, double* delta,
                           const double* delta0, double* partials, SolverState* st, cudaStream_t s);
 void launch_norms(const Grid& g, const double* v, int comps, double* partials, unsigned int* counter,

@@ -148,211 +148,13 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd
   }
 }
 
-// ---------------------------------------------------------------------------
-// One NBJM sweep (Algorithm 2 inner step): theta_out = Phi~^-1 tau.
-//
-// Phi~ is block diagonal with one block Phi_bar_{v,t} per (column pair v,
-// time t) (Section IV-B).  A group of GS lanes solves one block; lane a owns
-// unknown a = jj*NS + k of each pair-row (node (i, 2v+jj), component k).  The
-// groups of a block run over consecutive t, which share the factor of their
-// time class.  Per pair-row i:
-//   forward:  y_i = L0_i^-1 (tau_i - L1_i y_{i-1} - L2_i y_{i-2})
-//   backward: x_i = L0_i^-T (y_i - L1_{i+1}' x_{i+1} - L2_{i+2}' x_{i+2})
-// y is kept in theta_out between the two passes.  At t = 0, Phi_bar = Q^-1
-// node by node, so theta = Q tau.
-// ---------------------------------------------------------------------------
-template <int NS>
-struct SweepGeom {
-  static constexpr int G2 = 2 * NS;
-  static constexpr int GS = G2 <= 2 ? 2 : G2 <= 4 ? 4 : G2 <= 8 ? 8 : G2 <= 16 ? 16 : 32;
-  static constexpr int BS = G2 * G2;
-};
+}  // namespace hot
+}  // namespace lq2d
 
-template <int NS, int VAR, typename VT>
-__global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
-                                                                   SolverState* st) {
-  // VT = float is the mixed mode: FP32 factors, blocks and iterates, with
-  // the flexible (Polak-Ribiere) ratio for the next direction
-  constexpr bool FLEX = sizeof(VT) == 4;
-  constexpr bool UPDATE = VAR == kSweepUpdate;
-  constexpr bool XI = VAR == kSweepXi;
-  constexpr bool OMEGA = VAR == kSweepOmega || VAR == kSweepOmegaMu;
-  constexpr bool MU = VAR == kSweepOmegaMu;
-  constexpr int G2 = SweepGeom<NS>::G2, GS = SweepGeom<NS>::GS, BS = SweepGeom<NS>::BS;
-  if (st != nullptr && st->done) return;
-  const int lane32 = threadIdx.x & 31;
-  const int al = threadIdx.x & (GS - 1);
-  const unsigned gmask = GS == 32 ? 0xffffffffu : (((1u << GS) - 1u) << (lane32 & ~(GS - 1)));
-  const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / GS;
-  const int Tp = g.T + 1;
-  const bool active = gid < (long long)g.V * Tp;
-  const int v = active ? (int)(gid / Tp) : 0;
-  const int t = active ? (int)(gid % Tp) : 0;
-  const int ac = al < G2 ? al : 0;
-  const int jj = ac / NS, k = ac % NS;
-  const int j = 2 * v + jj;
-  const bool node_ok = active && al < G2 && j < g.N;
-  const long long kP = (long long)k * g.Ps;
-  const double vth = UPDATE ? st->theta : 0.0;
-  const bool flex_dot = FLEX && MU && st->have_mu;  // q'y is needed only after the first step
-  double acc0 = 0.0, acc1 = 0.0;
+#include "sweep_tiled.cuh"
 
-  if (active) {
-    const int cls = (t == g.T) ? 1 : 0;
-    const VT* fac = pd.fac + (size_t)(2 * v + cls) * pd.fac_vc;
-    VT ym1[G2], ym2[G2];
-#pragma unroll
-    for (int b = 0; b < G2; ++b) { ym1[b] = VT(0); ym2[b] = VT(0); }
-    for (int i = 0; i < g.K; ++i) {
-      const int p = i * g.N + j;
-      const long long off = node_ok ? (long long)p * Tp + t : 0;
-      VT tau = VT(0);
-      if (node_ok) {
-        if (UPDATE) {
-          const double rr = a.r[kP + off] - vth * a.y[kP + off];
-          a.r[kP + off] = rr;
-          a.delta[kP + off] += vth * a.d[kP + off];
-          tau = (VT)rr;
-          acc0 += rr * rr;
-          acc1 = fmax(acc1, fabs(rr));
-        } else {
-          tau = (VT)a.src[kP + off];
-        }
-        if (XI) {
-          // (Xi~ delta)_t = A_hat Q^-1 delta_{t-1} + Q^-1 A_hat' delta_{t+1}
-#pragma unroll
-          for (int dir = 0; dir < 5; ++dir) {
-            const int r = nbr_node(i, j, dir, g.K, g.N);
-            if (r < 0) continue;
-            const long long rb = (long long)r * Tp + t;
-            if (t >= 1) {
-              const VT* blk = pd.AQ + (((size_t)p * 5 + dir) * NS + k) * NS;
-#pragma unroll
-              for (int c = 0; c < NS; ++c) tau += blk[c] * a.delta_s[c * g.Ps + rb - 1];
-            }
-            if (t < g.T) {
-              const VT* blk = pd.QAt + (((size_t)p * 5 + dir) * NS + k) * NS;
-#pragma unroll
-              for (int c = 0; c < NS; ++c) tau += blk[c] * a.delta_s[c * g.Ps + rb + 1];
-            }
-          }
-          a.rtheta_out[kP + off] = (double)tau;
-        }
-        if (OMEGA && t >= 1) {
-#pragma unroll
-          for (int o = 0; o < 5; ++o) {
-            const int qn = offpair_node(i, j, o, g.K, g.N);
-            if (qn < 0) continue;
-            const VT* blk = pd.Om + (((size_t)p * 5 + o) * NS + k) * NS;
-            const long long qb = (long long)qn * Tp + t;
-#pragma unroll
-            for (int c = 0; c < NS; ++c) tau += blk[c] * a.theta_in[c * g.Ps + qb];
-          }
-        }
-      }
-      if (t == 0) {
-        // Phi_bar_{v,0} = blkdiag(Q^-1): theta = Q tau, node by node
-        VT out = VT(0);
-        const VT* Qrow = pd.Qm + ((size_t)p * NS + k) * NS;
-#pragma unroll
-        for (int c = 0; c < NS; ++c) {
-          const VT tc = __shfl_sync(gmask, tau, jj * NS + c, GS);
-          if (node_ok) out += Qrow[c] * tc;
-        }
-        if (node_ok) {
-          a.theta_out[kP + off] = out;
-          if (MU) acc0 += (double)out * a.r[kP + off];
-          if (flex_dot) acc1 += (double)out * a.y[kP + off];
-        }
-        continue;
-      }
-      // forward substitution over pair-row i
-      const VT* rec = fac + (size_t)i * pd.fac_rec;
-      VT w = tau;
-      if (i >= 1) {
-#pragma unroll
-        for (int b = 0; b < G2; ++b) w -= rec[BS + b * G2 + ac] * ym1[b];
-      }
-      if (i >= 2) {
-#pragma unroll
-        for (int b = 0; b < G2; ++b) w -= rec[b * G2 + ac] * ym2[b];
-      }
-      VT yv = VT(0);
-#pragma unroll
-      for (int b = 0; b < G2; ++b) yv += rec[2 * BS + b * G2 + ac] * __shfl_sync(gmask, w, b, GS);
-      if (node_ok) a.theta_out[kP + off] = yv;
-#pragma unroll
-      for (int b = 0; b < G2; ++b) {
-        ym2[b] = ym1[b];
-        ym1[b] = __shfl_sync(gmask, yv, b, GS);
-      }
-    }
-    if (t >= 1) {
-      VT xp1[G2], xp2[G2];
-#pragma unroll
-      for (int b = 0; b < G2; ++b) { xp1[b] = VT(0); xp2[b] = VT(0); }
-      for (int i = g.K - 1; i >= 0; --i) {
-        const int p = i * g.N + j;
-        const long long off = node_ok ? (long long)p * Tp + t : 0;
-        const VT* rec = fac + (size_t)i * pd.fac_rec;
-        VT w = node_ok ? a.theta_out[kP + off] : VT(0);
-        if (i + 1 < g.K) {
-          const VT* r1 = rec + pd.fac_rec;
-#pragma unroll
-          for (int b = 0; b < G2; ++b) w -= r1[4 * BS + b * G2 + ac] * xp1[b];
-        }
-        if (i + 2 < g.K) {
-          const VT* r2 = rec + 2 * pd.fac_rec;
-#pragma unroll
-          for (int b = 0; b < G2; ++b) w -= r2[3 * BS + b * G2 + ac] * xp2[b];
-        }
-        VT xv = VT(0);
-#pragma unroll
-        for (int b = 0; b < G2; ++b) xv += rec[5 * BS + b * G2 + ac] * __shfl_sync(gmask, w, b, GS);
-        if (node_ok) {
-          a.theta_out[kP + off] = xv;
-          if (MU) acc0 += (double)xv * a.r[kP + off];
-          if (flex_dot) acc1 += (double)xv * a.y[kP + off];
-        }
-#pragma unroll
-        for (int b = 0; b < G2; ++b) {
-          xp2[b] = xp1[b];
-          xp1[b] = __shfl_sync(gmask, xv, b, GS);
-        }
-      }
-    }
-  }
-  if (UPDATE) {
-    double tot0, tot1;
-    if (grid_reduce2<true>(acc0, acc1, a.partials, &st->counters[kCntNorm], &tot0, &tot1)) {
-      // Algorithm 1 line 11, with the stop rule selected by stop_mode
-      st->rnorm2 = tot0;
-      st->rnorm_inf = tot1;
-      const int it = st->iter + 1;
-      st->iter = it;
-      const bool pass = st->stop_mode == 0 ? (tot0 <= st->stop_bound) : (tot1 < st->stop_bound);
-      if (!isfinite(tot0)) st->done = kBreakdown;
-      else if (pass) st->done = kConverged;
-      else if (it >= st->max_iter) st->done = kMaxIter;
-    }
-  }
-  if (MU) {
-    double tot0, tot1;
-    if (grid_reduce2<false>(acc0, acc1, a.partials, &st->counters[kCntMu], &tot0, &tot1)) {
-      // Algorithm 1 lines 13-14: mu^(i+1) and the ratio used for d^(i+1);
-      // the mixed mode takes q^(i+1)'(r^(i+1) - r^(i)) / mu^(i), which equals
-      // mu^(i+1) / mu^(i) for an exactly symmetric preconditioner
-      if (!(tot0 > 0.0) || !isfinite(tot0) || !isfinite(tot1)) {
-        st->done = kBreakdown;
-      } else {
-        if (!st->have_mu) st->beta = 0.0;
-        else st->beta = FLEX ? (-st->theta * tot1) / st->mu : tot0 / st->mu;
-        st->mu = tot0;
-        st->have_mu = 1;
-      }
-    }
-  }
-}
+namespace lq2d {
+namespace hot {
 
 // ---------------------------------------------------------------------------
 // Recovery check (Section II-B): the full KKT residual of (x, u, delta) and
@@ -471,18 +273,48 @@ void launch_delta_y(const Grid& g, const NodeData& nd, const double* z, const QT
 template <int NS, typename VT>
 void launch_sweep(int variant, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a, SolverState* st,
                   cudaStream_t s) {
-  constexpr int GS = SweepGeom<NS>::GS;
-  const long long threads = (long long)g.V * (g.T + 1) * GS;
-  const unsigned blocks = (unsigned)((threads + kSweepThreads - 1) / kSweepThreads);
+  const unsigned blocks = sweep_blocks<NS>(g);
+  const size_t shm = sweep_smem_bytes<NS, VT>();
   switch (variant) {
-    case kSweepPlain: nbjm_sweep_kernel<NS, kSweepPlain, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
-    case kSweepUpdate: nbjm_sweep_kernel<NS, kSweepUpdate, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
-    case kSweepOmega: nbjm_sweep_kernel<NS, kSweepOmega, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
-    case kSweepOmegaMu:
-      nbjm_sweep_kernel<NS, kSweepOmegaMu, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st);
+    case kSweepPlain: nbjm_sweep_kernel<NS, kSweepPlain, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st); break;
+    case kSweepUpdate:
+      nbjm_sweep_kernel<NS, kSweepUpdate, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st);
       break;
-    default: nbjm_sweep_kernel<NS, kSweepXi, VT><<<blocks, kSweepThreads, 0, s>>>(g, pd, a, st); break;
+    case kSweepOmega: nbjm_sweep_kernel<NS, kSweepOmega, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st); break;
+    case kSweepOmegaMu:
+      nbjm_sweep_kernel<NS, kSweepOmegaMu, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st);
+      break;
+    case kSweepXiOmega:
+      nbjm_sweep_kernel<NS, kSweepXiOmega, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st);
+      break;
+    default: nbjm_sweep_kernel<NS, kSweepXi, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st); break;
   }
+}
+
+// Allows every sweep instantiation its shared-memory footprint (above the
+// 48 KB default for n >= 8 in FP64); called once per device before use.
+template <int NS, typename VT>
+cudaError_t prepare_sweeps_t() {
+  const int shm = (int)sweep_smem_bytes<NS, VT>();
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+    if (r != cudaSuccess) e = r;
+  };
+  set((const void*)nbjm_sweep_kernel<NS, kSweepPlain, VT>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepUpdate, VT>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepOmega, VT>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepOmegaMu, VT>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepXi, VT>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepXiOmega, VT>);
+  return e;
+}
+
+template <int NS>
+cudaError_t prepare_sweeps() {
+  cudaError_t e = prepare_sweeps_t<NS, double>();
+  cudaError_t f = prepare_sweeps_t<NS, float>();
+  return e != cudaSuccess ? e : f;
 }
 
 template <int NS>
@@ -497,7 +329,7 @@ const KernelTable* make_table() {
   static const KernelTable t = {&launch_delta_z<NS, double>, &launch_delta_z<NS, float>,
                                 &launch_delta_y<NS, double>, &launch_delta_y<NS, float>,
                                 &launch_sweep<NS, double>,   &launch_sweep<NS, float>,
-                                &launch_kkt<NS>};
+                                &launch_kkt<NS>, &prepare_sweeps<NS>};
   return &t;
 }
 

@@ -31,7 +31,7 @@ const KernelTable* kernel_table(int n) {
 namespace {
 
 __global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
-                                  int keep_iter) {
+                                  int keep_iter, double* hist, int hist_cap) {
   st->mu = 0.0;
   st->beta = 0.0;
   st->ydot = 0.0;
@@ -45,7 +45,84 @@ __global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int
   st->have_mu = 0;
   st->body_count = 0;
   st->body_cap = max_iter + 2;
+  st->hist = hist;
+  st->hist_cap = hist_cap;
   for (int c = 0; c < 8; ++c) st->counters[c] = 0u;
+}
+
+// Identity preconditioner (plain CG, used to estimate kappa(Delta)): q = r
+// and mu = r'r.  With UPDATE, Algorithm 1 lines 9-11 come first (delta +=
+// vartheta d, r -= vartheta y, stop test), and mu is the new ||r||^2.
+template <bool UPDATE>
+__global__ void ident_kernel(Grid g, double* __restrict__ r, double* __restrict__ delta,
+                             const double* __restrict__ y, const double* __restrict__ d, double* __restrict__ q,
+                             double* partials, SolverState* st) {
+  if (st->done) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double vth = UPDATE ? st->theta : 0.0;
+  double s2 = 0.0, mx = 0.0;
+  if (idx < g.P) {
+    for (int k = 0; k < g.n; ++k) {
+      const long long e = k * g.Ps + idx;
+      double rv = r[e];
+      if (UPDATE) {
+        rv -= vth * y[e];
+        r[e] = rv;
+        delta[e] += vth * d[e];
+      }
+      q[e] = rv;
+      s2 += rv * rv;
+      mx = fmax(mx, fabs(rv));
+    }
+  }
+  double t0, t1;
+  if (grid_reduce2<true>(s2, mx, partials, &st->counters[UPDATE ? kCntNorm : kCntMu], &t0, &t1)) {
+    if (UPDATE) {
+      st->rnorm2 = t0;
+      st->rnorm_inf = t1;
+      const int it = st->iter + 1;
+      st->iter = it;
+      record_theta(st, it - 1);
+      const bool pass = st->stop_mode == 0 ? (t0 <= st->stop_bound) : (t1 < st->stop_bound);
+      if (!isfinite(t0)) { st->done = kBreakdown; return; }
+      if (pass) { st->done = kConverged; return; }
+      if (it >= st->max_iter) { st->done = kMaxIter; return; }
+    }
+    if (!(t0 > 0.0)) { st->done = kBreakdown; return; }
+    if (!st->have_mu) {
+      st->beta = 0.0;
+    } else {
+      st->beta = t0 / st->mu;
+      record_beta(st, st->iter - 1);
+    }
+    st->mu = t0;
+    st->have_mu = 1;
+  }
+}
+
+// Exit test of the standalone NBJM solver (Algorithm 2's last line):
+// ||a - b||_inf < eps, b = NULL meaning zero; counts the outer step.
+template <typename VT>
+__global__ void nbjm_diff_kernel(Grid g, const VT* __restrict__ a, const VT* __restrict__ b, double* partials,
+                                 SolverState* st) {
+  if (st->done) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0;
+  if (idx < g.P)
+    for (int k = 0; k < g.n; ++k) {
+      const long long e = k * g.Ps + idx;
+      const double dv = (double)a[e] - (b != nullptr ? (double)b[e] : 0.0);
+      mx = fmax(mx, fabs(dv));
+    }
+  double t0, t1;
+  if (grid_reduce2<true>(0.0, mx, partials, &st->counters[kCntNorm], &t0, &t1)) {
+    const int it = st->iter + 1;
+    st->iter = it;
+    st->rnorm_inf = t1;
+    if (!isfinite(t1)) st->done = kBreakdown;
+    else if (t1 < st->stop_bound) st->done = kConverged;
+    else if (it >= st->max_iter) st->done = kMaxIter;
+  }
 }
 
 // r^(0) = r_delta - Delta delta^(0) (Algorithm 1 line 2) with y = Delta delta^(0)
@@ -174,8 +251,26 @@ inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + th
 }  // namespace
 
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
-                       int keep_iter, cudaStream_t s) {
-  init_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, stop_mode, bnorm2, keep_iter);
+                       int keep_iter, double* hist, int hist_cap, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, stop_mode, bnorm2, keep_iter, hist, hist_cap);
+}
+
+void launch_ident(const Grid& g, bool update, double* r, double* delta, const double* y, const double* d,
+                  double* q, double* partials, SolverState* st, cudaStream_t s) {
+  if (update)
+    ident_kernel<true><<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, r, delta, y, d, q, partials, st);
+  else
+    ident_kernel<false><<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, r, delta, y, d, q, partials, st);
+}
+
+void launch_nbjm_diff(const Grid& g, const void* a, const void* b, int fp32, double* partials, SolverState* st,
+                      cudaStream_t s) {
+  if (fp32)
+    nbjm_diff_kernel<float><<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(
+        g, static_cast<const float*>(a), static_cast<const float*>(b), partials, st);
+  else
+    nbjm_diff_kernel<double><<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(
+        g, static_cast<const double*>(a), static_cast<const double*>(b), partials, st);
 }
 
 void launch_init_residual(const Grid& g, const double* rhs, const double* y, double* r, double* delta,

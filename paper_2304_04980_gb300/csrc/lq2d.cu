@@ -1,5 +1,6 @@
 // C-ABI library: problem handle, setup, and the PCG driver (Algorithm 1 with
 // Algorithm 2 as preconditioner) over the CUDA kernels of this directory.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,12 +31,13 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 struct GraphEntry {
-  int S = 0, L = 0, precision = 0;
+  int S = 0, L = 0, precision = 0, precond = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
 constexpr int kMaxGraphs = 8;
+constexpr int kHistCap = 1 << 16;  // PCG steps whose coefficients are kept for the Lanczos estimate
 constexpr int kStreamChunk = 4;  // steps enqueued between stop-flag reads (driver 1)
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
@@ -80,6 +82,10 @@ struct lq2d_problem {
   PrecData<double> pd64{};
   PrecData<float> pd32{};
   float* f32_buf = nullptr;  // FP32 copies of the factors and node blocks (mode 1, allocated on first use)
+  int precond_kind = 0;      // 0: NBJM (Algorithm 2), 1: none (plain CG)
+  int kappa = 0;             // record the PCG coefficients and estimate the condition number
+  double* hist = nullptr;    // device: vartheta_j, beta_j pairs
+  std::vector<double> h_hist;
   int graph_body_kernels = 0;  // kernels per device-loop body of the last graph launch (0: no graph)
 };
 
@@ -135,6 +141,7 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   g.Pus = round_up(g.Pu, 64);
   h->kt = kernel_table(n);
   if (!h->kt) return fail(LQ2D_EINVAL, "no kernels for this n");
+  LQ_CUDA(h->kt->prepare());
   LQ_CUDA(cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking));
   const size_t NN = g.NN, nn = (size_t)n * n;
   int rc;
@@ -339,6 +346,10 @@ const void* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, boo
   return enqueue_precond_t<double>(h, S, L, fuse_update, mu, st, r_in, s, timing);
 }
 
+// The preconditioner output q is FP32 only for the NBJM preconditioner in
+// the mixed mode; the identity preconditioner copies r in FP64.
+bool q_is_f32(const lq2d_problem* h) { return h->precision == 1 && h->precond_kind == 0; }
+
 // y = Delta dn with dn = q + beta d_old; q is the preconditioner output in
 // the preconditioner's precision.
 void enqueue_delta(lq2d_problem* h, const void* q, const double* dold, double* dout, double* y,
@@ -354,7 +365,7 @@ void enqueue_delta(lq2d_problem* h, const void* q, const double* dold, double* d
     e1 = h->ev_pool[k + 1];
     cudaEventRecord(e0, s);
   }
-  if (h->precision == 1) {
+  if (q_is_f32(h)) {
     const float* qf = static_cast<const float*>(q);
     h->kt->delta_z_f32(h->g, h->nd, qf, dold, h->z, st, loop ? 1 : 0, s);
     h->kt->delta_y_f32(h->g, h->nd, h->z, qf, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
@@ -372,12 +383,30 @@ void enqueue_delta(lq2d_problem* h, const void* q, const double* dold, double* d
 // sweep and mu into its last.
 void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
   enqueue_delta(h, h->thB, h->d, h->d, h->y, h->st, true, s, timing);
+  if (h->precond_kind == 1) {
+    cudaEvent_t e1 = nullptr;
+    if (timing) {
+      const size_t k = h->ev_pool.size();
+      h->ev_pool.resize(k + 2);
+      cudaEventCreate(&h->ev_pool[k]);
+      cudaEventCreate(&h->ev_pool[k + 1]);
+      cudaEventRecord(h->ev_pool[k], s);
+      e1 = h->ev_pool[k + 1];
+    }
+    launch_ident(h->g, true, h->r, h->delta, h->y, h->d, h->thB, h->partials, h->st, s);
+    h->launches += 1;
+    if (timing) cudaEventRecord(e1, s);
+    return;
+  }
   enqueue_precond(h, S, L, true, true, h->st, h->r, s, timing);
 }
 
+int sweeps_per_step(const lq2d_problem* h, int S, int L) { return h->precond_kind == 1 ? 1 : S * L; }
+
 int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   for (int i = 0; i < h->ngraphs; ++i)
-    if (h->graphs[i].S == S && h->graphs[i].L == L && h->graphs[i].precision == h->precision) {
+    if (h->graphs[i].S == S && h->graphs[i].L == L && h->graphs[i].precision == h->precision &&
+        h->graphs[i].precond == h->precond_kind) {
       *exec = h->graphs[i].exec;
       return LQ2D_OK;
     }
@@ -391,6 +420,7 @@ int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   ge.S = S;
   ge.L = L;
   ge.precision = h->precision;
+  ge.precond = h->precond_kind;
   LQ_CUDA(cudaGraphCreate(&ge.graph, 0));
   cudaGraphConditionalHandle hc;
   LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, ge.graph, 1u, cudaGraphCondAssignDefault));
@@ -433,7 +463,7 @@ int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
     int rc = get_graph(h, S, L, &exec);
     if (rc) return rc;
     LQ_CUDA(cudaGraphLaunch(exec, s));
-    h->graph_body_kernels = 2 + S * L + 1;
+    h->graph_body_kernels = 2 + sweeps_per_step(h, S, L) + 1;
     return LQ2D_OK;
   }
   // driver 1: steps enqueued from the host in chunks; the stop flag of the
@@ -470,8 +500,8 @@ int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
 // around the Delta apply, then S*L pairs around the sweeps.  Only launches
 // that did work are counted: in the step that met the stop test the sweeps
 // after the first return at once, and later steps are empty.
-void collect_timing(lq2d_problem* h, int S, int L, int steps_done) {
-  const size_t per = 2 + 2 * (size_t)S * L;
+void collect_timing(lq2d_problem* h, int sweeps, int steps_done) {
+  const size_t per = 2 + 2 * (size_t)sweeps;
   const size_t steps = h->ev_pool.size() / per;
   for (size_t k = 0; k < steps && (int)k < steps_done; ++k) {
     const size_t b = k * per;
@@ -481,7 +511,7 @@ void collect_timing(lq2d_problem* h, int S, int L, int steps_done) {
       h->stats.delta_ms += ms;
       h->stats.delta_launches += 1;
     }
-    const size_t nsw = last ? 1 : (size_t)S * L;
+    const size_t nsw = last ? 1 : (size_t)sweeps;
     for (size_t w = 0; w < nsw; ++w) {
       if (cudaEventElapsedTime(&ms, h->ev_pool[b + 2 + 2 * w], h->ev_pool[b + 3 + 2 * w]) == cudaSuccess) {
         h->stats.sweep_ms += ms;
@@ -491,6 +521,67 @@ void collect_timing(lq2d_problem* h, int S, int L, int steps_done) {
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e2 = squared
+// off-diagonal) below x (Sturm sequence).
+int sturm_below(const std::vector<double>& d, const std::vector<double>& e2, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    q = d[i] - x - (i ? e2[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+// k-th smallest eigenvalue by bisection inside [lo, hi].
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e2, int k, double lo, double hi) {
+  for (int it = 0; it < 200 && hi - lo > 1e-13 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(d, e2, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Extreme Ritz values of the preconditioned operator from the recorded PCG
+// coefficients: the Lanczos matrix has diagonal 1/a_0, 1/a_j + b_{j-1}/a_{j-1}
+// and off-diagonal sqrt(b_j)/a_j (CG-Lanczos relation; the paper reports
+// kappa(P_S^-1/2 Delta P_S^-1/2) in Section V).
+void lanczos_estimate(lq2d_problem* h, int iterations, cudaStream_t s) {
+  const int m = std::min(iterations, kHistCap);
+  h->stats.kappa_estimate = 0.0;
+  h->stats.lambda_min = 0.0;
+  h->stats.lambda_max = 0.0;
+  if (m < 1) return;
+  h->h_hist.assign(2 * (size_t)m, 0.0);
+  if (cudaMemcpyAsync(h->h_hist.data(), h->hist, 2 * (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return;
+  std::vector<double> d(m), e2(m > 1 ? m - 1 : 0);
+  for (int j = 0; j < m; ++j) {
+    const double a = h->h_hist[2 * j];
+    d[j] = 1.0 / a;
+    if (j > 0) {
+      const double ap = h->h_hist[2 * (j - 1)], bp = h->h_hist[2 * (j - 1) + 1];
+      d[j] += bp / ap;
+      e2[j - 1] = bp / (ap * ap);
+    }
+  }
+  double lo = d[0], hi = d[0];
+  for (int j = 0; j < m; ++j) {
+    const double r = (j > 0 ? std::sqrt(e2[j - 1]) : 0.0) + (j + 1 < m ? std::sqrt(e2[j]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  const double lmin = tridiag_eig(d, e2, 0, lo, hi);
+  const double lmax = tridiag_eig(d, e2, m - 1, lo, hi);
+  h->stats.lambda_min = lmin;
+  h->stats.lambda_max = lmax;
+  h->stats.kappa_estimate = lmin > 0.0 ? lmax / lmin : 0.0;
 }
 
 // The full solve on device buffers (host layout), ordered on s.
@@ -504,7 +595,11 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
   const KernelTable* kt = h->kt;
   std::memset(&h->stats, 0, sizeof(h->stats));
   h->ev_pool.clear();
-  launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, s);
+  if (h->kappa && !h->hist) {
+    int rc = dev_alloc(h, &h->hist, 2 * (size_t)kHistCap);
+    if (rc) return rc;
+  }
+  launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, h->kappa ? h->hist : nullptr, kHistCap, s);
   h->launches += 2;  // state and initial residual
   if (d_delta0) {
     h->launches += 3;
@@ -520,7 +615,12 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
   double rel = 0.0;
   int iter_before = 0;
   for (;;) {
-    enqueue_precond(h, S, L, false, true, h->st, h->r, s, false);
+    if (h->precond_kind == 1) {
+      launch_ident(g, false, h->r, h->delta, h->y, h->d, h->thB, h->partials, h->st, s);
+      h->launches += 1;
+    } else {
+      enqueue_precond(h, S, L, false, true, h->st, h->r, s, false);
+    }
     LQ_CUDA(cudaMemsetAsync(h->d, 0, (size_t)g.Ps * g.n * sizeof(double), s));
     h->graph_body_kernels = 0;
     int rc = run_loop(h, S, L, max_iter, s);
@@ -537,7 +637,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     LQ_CUDA(cudaGetLastError());
     const SolverState& hs = *h->h_st;
     h->launches += (long long)hs.body_count * h->graph_body_kernels;
-    if (h->timing) collect_timing(h, S, L, hs.iter - iter_before);
+    if (h->timing) collect_timing(h, sweeps_per_step(h, S, L), hs.iter - iter_before);
     iter_before = hs.iter;
     const double bn = std::sqrt(hs.bnorm2);
     rel = bn > 0 ? std::sqrt(h->h_kkt[0]) / bn : std::sqrt(h->h_kkt[0]);
@@ -547,7 +647,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
       // from the current iterate with r = r_delta - Delta delta
       ++restarts;
       h->launches += 4;
-      launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 1, s);
+      launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 1, nullptr, 0, s);
       kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
       kt->delta_y(g, h->nd, h->z, h->delta, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
       launch_init_residual(g, h->rhs, h->y, h->r, h->delta, h->delta, h->partials, h->st, s);
@@ -568,6 +668,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     h->stats.cost = 0.5 * h->h_kkt[1];
     h->stats.status = status;
     h->stats.body_executions = hs.body_count;
+    if (h->kappa) lanczos_estimate(h, hs.iter, s);
     break;
   }
   if (d_x) launch_to_api(h->z, d_x, g.NN, g.T + 1, g.n, g.Ps, s);
@@ -582,6 +683,138 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
   if (status == LQ2D_EBREAKDOWN) return fail(status, "breakdown: y'd <= 0 or a non-finite scalar");
   if (status == LQ2D_ETIMEOUT) return fail(status, "device loop cap reached");
   if (status != LQ2D_OK) return fail(status, "solver state not set");
+  return LQ2D_OK;
+}
+
+// Buffer that holds delta^(s) after `steps` outer steps of the standalone
+// NBJM solver (-1: none yet, delta^(0) = 0).  Buffers 0..2 rotate: each step
+// writes its L sweeps alternately into the two buffers other than the
+// current iterate, the last one into the second of them.
+int nbjm_buffer_after(int steps, int L) {
+  int cur = -1;
+  for (int k = 0; k < steps; ++k) {
+    int others[2];
+    int c = 0;
+    for (int b = 0; b < 3 && c < 2; ++b)
+      if (b != cur) others[c++] = b;
+    cur = others[(L - 1) & 1];
+  }
+  return cur;
+}
+
+// One outer step of Algorithm 2 as a solver: L sweeps, the first started
+// from the outer iterate (tau = r_delta + Xi~ delta + Omega~ delta, reading
+// A22), then the exit test on ||delta^(s+1) - delta^(s)||_inf.
+template <typename VT>
+void enqueue_nbjm_outer(lq2d_problem* h, int L, int step, cudaStream_t s) {
+  VT* B[3] = {reinterpret_cast<VT*>(h->thA), reinterpret_cast<VT*>(h->thB), reinterpret_cast<VT*>(h->z)};
+  const int cur = nbjm_buffer_after(step, L);
+  int others[2];
+  int c = 0;
+  for (int b = 0; b < 3 && c < 2; ++b)
+    if (b != cur) others[c++] = b;
+  const VT* prev = nullptr;
+  for (int l = 0; l < L; ++l) {
+    SweepArgsT<VT> a{};
+    a.partials = h->partials;
+    a.theta_out = B[others[l & 1]];
+    a.y = h->y;
+    a.r = h->rhs;
+    int variant;
+    if (l == 0 && cur < 0) {
+      variant = kSweepPlain;
+      a.src = h->rhs;
+    } else if (l == 0) {
+      variant = kSweepXiOmega;
+      a.src = h->rhs;
+      a.delta_s = B[cur];
+      a.theta_in = B[cur];
+      a.rtheta_out = h->rth;
+    } else {
+      variant = kSweepOmega;
+      a.src = cur < 0 ? h->rhs : h->rth;
+      a.theta_in = prev;
+    }
+    if constexpr (sizeof(VT) == 4)
+      h->kt->sweep_f32(variant, h->g, h->pd32, a, h->st, s);
+    else
+      h->kt->sweep(variant, h->g, h->pd64, a, h->st, s);
+    prev = B[others[l & 1]];
+  }
+  launch_nbjm_diff(h->g, prev, cur < 0 ? nullptr : B[cur], sizeof(VT) == 4, h->partials, h->st, s);
+  h->launches += L + 1;
+}
+
+int solve_nbjm_impl(lq2d_problem* h, double eps, int L, int max_outer, double* d_x, double* d_u,
+                    double* d_costate, int* outer, double* rel_kkt, cudaStream_t s) {
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(LQ2D_EINVAL, "eps must be positive and finite");
+  if (L < 1) return fail(LQ2D_EINVAL, "inner_L must be >= 1");
+  if (max_outer < 1) return fail(LQ2D_EINVAL, "max_outer must be >= 1");
+  const Grid& g = h->g;
+  const bool f32 = h->precision == 1;
+  std::memset(&h->stats, 0, sizeof(h->stats));
+  launch_init_state(h->st, eps, max_outer, 1, h->bnorm, 0, nullptr, 0, s);
+  h->launches += 1;
+  cudaEvent_t flag_ev[2];
+  LQ_CUDA(cudaEventCreateWithFlags(&flag_ev[0], cudaEventDisableTiming));
+  LQ_CUDA(cudaEventCreateWithFlags(&flag_ev[1], cudaEventDisableTiming));
+  bool pending[2] = {false, false};
+  int slot = 0, enq = 0;
+  while (enq < max_outer) {
+    for (int c = 0; c < kStreamChunk * 4 && enq < max_outer; ++c, ++enq) {
+      if (f32) enqueue_nbjm_outer<float>(h, L, enq, s);
+      else enqueue_nbjm_outer<double>(h, L, enq, s);
+    }
+    cudaMemcpyAsync(&h->h_done[slot], &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(flag_ev[slot], s);
+    pending[slot] = true;
+    slot ^= 1;
+    if (pending[slot]) {
+      cudaEventSynchronize(flag_ev[slot]);
+      pending[slot] = false;
+      if (h->h_done[slot] != 0) break;
+    }
+  }
+  cudaEventDestroy(flag_ev[0]);
+  cudaEventDestroy(flag_ev[1]);
+  LQ_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  const int steps = h->h_st->iter;
+  const int done = h->h_st->done;
+  const int buf = nbjm_buffer_after(steps, L);
+  double* B64[3] = {h->thA, h->thB, h->z};
+  if (buf >= 0) {
+    if (f32) launch_to_f64(reinterpret_cast<const float*>(B64[buf]), h->delta, (long long)g.Ps * g.n, s);
+    else LQ_CUDA(cudaMemcpyAsync(h->delta, B64[buf], (size_t)g.Ps * g.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    LQ_CUDA(cudaMemsetAsync(h->delta, 0, (size_t)g.Ps * g.n * sizeof(double), s));
+  }
+  // recovery (Section II-B) and the true KKT residual of the result
+  h->kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
+  launch_recover_u(g, h->nd, h->delta, h->u, s);
+  h->kt->kkt(g, h->nd, h->z, h->u, h->delta, h->rhs, h->partials, h->st, h->kkt_out, s);
+  h->launches += 3 + (f32 ? 1 : 0);
+  LQ_CUDA(cudaMemcpyAsync(h->h_kkt, h->kkt_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (d_x) launch_to_api(h->z, d_x, g.NN, g.T + 1, g.n, g.Ps, s);
+  if (d_u) launch_to_api(h->u, d_u, g.NN, g.T, g.m, g.Pus, s);
+  if (d_costate) launch_to_api(h->delta, d_costate, g.NN, g.T + 1, g.n, g.Ps, s);
+  h->launches += (d_x != nullptr) + (d_u != nullptr) + (d_costate != nullptr);
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  const double bn = std::sqrt(h->h_st->bnorm2);
+  const double rel = bn > 0 ? std::sqrt(h->h_kkt[0]) / bn : std::sqrt(h->h_kkt[0]);
+  h->stats.outer_iterations = steps;
+  h->stats.rel_kkt_residual = rel;
+  h->stats.kkt_inf = h->h_kkt[2];
+  h->stats.cost = 0.5 * h->h_kkt[1];
+  h->stats.rel_residual = h->h_st->rnorm_inf;  // last change ||delta^(s+1) - delta^(s)||_inf
+  if (outer) *outer = steps;
+  if (rel_kkt) *rel_kkt = rel;
+  int status = done == kConverged ? LQ2D_OK : done == kMaxIter ? LQ2D_ENOCONV : LQ2D_EBREAKDOWN;
+  h->stats.status = status;
+  if (status == LQ2D_ENOCONV) return fail(status, "max_outer reached before the exit test passed");
+  if (status == LQ2D_EBREAKDOWN) return fail(status, "non-finite iterate");
   return LQ2D_OK;
 }
 
@@ -744,6 +977,14 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
   return LQ2D_OK;
 }
 
+int lq2d_solve_nbjm_device(lq2d_problem* h, double eps, int inner_L, int max_outer, void* d_x, void* d_u,
+                           void* d_costate, int* outer_iterations, double* rel_kkt_residual, void* stream) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  return solve_nbjm_impl(h, eps, inner_L, max_outer, static_cast<double*>(d_x), static_cast<double*>(d_u),
+                         static_cast<double*>(d_costate), outer_iterations, rel_kkt_residual,
+                         static_cast<cudaStream_t>(stream));
+}
+
 int lq2d_set_option(lq2d_problem* h, int option, double value) {
   if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
   const int v = (int)value;
@@ -758,6 +999,13 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
       return LQ2D_OK;
     case LQ2D_OPT_TIMING:
       h->timing = v ? 1 : 0;
+      return LQ2D_OK;
+    case LQ2D_OPT_PRECONDITIONER:
+      if (v != 0 && v != 1) return fail(LQ2D_EINVAL, "preconditioner must be 0 (NBJM) or 1 (none)");
+      h->precond_kind = v;
+      return LQ2D_OK;
+    case LQ2D_OPT_KAPPA:
+      h->kappa = v ? 1 : 0;
       return LQ2D_OK;
     case LQ2D_OPT_MAX_RESTARTS:
       if (v < 0) return fail(LQ2D_EINVAL, "max restarts must be >= 0");

@@ -19,11 +19,11 @@ LIB_PATH = os.path.join(_PKG, "_lib", "liblq2d.so")
 OK, EINVAL, ENOTPD, ENOCONV, EBREAKDOWN, ECUDA, ENOMEM, ETIMEOUT = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ECUDA",
                 6: "ENOMEM", 7: "ETIMEOUT"}
-OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS = 1, 2, 3, 4
+OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS, OPT_PRECONDITIONER, OPT_KAPPA = 1, 2, 3, 4, 5, 6
 
 EXPORTED = (
     "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
-    "lq2d_solve_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_apply_delta_static",
+    "lq2d_solve_device", "lq2d_solve_nbjm_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_apply_delta_static",
     "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
 )
@@ -36,7 +36,9 @@ class Stats(ctypes.Structure):
         ("rel_residual", ctypes.c_double), ("rel_kkt_residual", ctypes.c_double),
         ("kkt_inf", ctypes.c_double), ("cost", ctypes.c_double),
         ("sweep_ms", ctypes.c_double), ("delta_ms", ctypes.c_double),
-        ("launches_total", ctypes.c_longlong), ("body_executions", ctypes.c_int), ("pad2", ctypes.c_int),
+        ("launches_total", ctypes.c_longlong), ("body_executions", ctypes.c_int),
+        ("outer_iterations", ctypes.c_int), ("kappa_estimate", ctypes.c_double),
+        ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -75,6 +77,7 @@ def load() -> ctypes.CDLL:
         "lq2d_set_affine": (i, [_vp, _vp]),
         "lq2d_solve": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp, _ip, _dp]),
         "lq2d_solve_device": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp, _ip, _dp, _vp]),
+        "lq2d_solve_nbjm_device": (i, [_vp, d, i, i, _vp, _vp, _vp, _ip, _dp, _vp]),
         "lq2d_apply_delta_device": (i, [_vp, _vp, _vp, _vp]),
         "lq2d_apply_precond_device": (i, [_vp, i, i, _vp, _vp, _vp]),
         "lq2d_apply_delta_static": (i, [i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -206,6 +209,16 @@ class Problem:
                                         _addr(costate), ctypes.byref(it), ctypes.byref(rel), _stream(stream))
         _check(code, allow)
         return dict(iterations=it.value, rel_kkt=rel.value, status=code)
+
+    def solve_nbjm_device(self, eps, L, max_outer, x=None, u=None, costate=None, stream=None,
+                          allow=(ENOCONV,)):
+        """Algorithm 2 run to its exit test (the paper's standard NBJM)."""
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        code = load().lq2d_solve_nbjm_device(self._h, eps, L, max_outer, _addr(x), _addr(u), _addr(costate),
+                                             ctypes.byref(it), ctypes.byref(rel), _stream(stream))
+        _check(code, allow)
+        return dict(outer_iterations=it.value, rel_kkt=rel.value, status=code)
 
     def apply_delta_device(self, d_in, d_out, stream=None):
         _check(load().lq2d_apply_delta_device(self._h, _addr(d_in), _addr(d_out), _stream(stream)))

@@ -47,7 +47,7 @@ def test_status_codes_match_header():
 
 def test_stats_struct_layout():
     from paper_2304_04980_gb300 import lq2d
-    assert ctypes.sizeof(lq2d.Stats) == 6 * 4 + 6 * 8 + 8 + 2 * 4
+    assert ctypes.sizeof(lq2d.Stats) == 6 * 4 + 6 * 8 + 8 + 2 * 4 + 3 * 8
 
 
 @pytest.mark.parametrize("dims", [(0, 4, 4, 2, 1), (4, 0, 4, 2, 1), (4, 4, 0, 2, 1), (4, 4, 4, 0, 1),
