@@ -50,12 +50,16 @@ def parse_args():
     ap.add_argument("--workload", default="grid64_T100", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--driver", choices=["graph", "stream"], default="graph")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
-                    help="fp64: FP64 everywhere; mixed: FP32 preconditioner, FP64 residual/dots/updates")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed2"], default="fp64",
+                    help="fp64: FP64 everywhere; mixed: FP32 preconditioner, FP64 residual/dots/updates; "
+                         "mixed2: also the product Delta d in FP32, with FP64 residual replacement per phase")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed mixed-precision comparison on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG steps in the CPU sample")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time the batched solve of this many uneven instances (K, N in 8..64, T in 50..200) "
+                         "against solving them one after another")
     return ap.parse_args()
 
 
@@ -344,8 +348,8 @@ def run_ours(args, dist):
     inputs = [torch.from_numpy(a).to(dev) for a in host]
     pinned = [torch.from_numpy(a).pin_memory() for a in host]
     prob = lq2d.Problem.from_device(g.K, g.N, g.T, g.n, g.m, *inputs, stream=stream)
-    if args.precision == "mixed":
-        prob.set_precision(1)
+    if args.precision != "fp64":
+        prob.set_precision(1 if args.precision == "mixed" else 2)
     if args.driver == "stream":
         prob.set_option(lq2d.OPT_DRIVER, 1)
     x = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
@@ -449,16 +453,18 @@ def run_ours(args, dist):
     # ---- the same workload in the other precision, same protocol (FP64 plain vs mixed)
     compare = None
     if not args.no_compare and args.precision == "fp64":
-        prob.set_precision(1)
-        for _ in range(args.warmup):
-            step()
-        c_ms, c_its, c_rels = timed(args.steps)
+        compare = []
+        for mode, label in ((1, "mixed: FP32 preconditioner, FP64 residual/dots/updates"),
+                            (2, "mixed2: FP32 preconditioner and Delta product, FP64 residual replacement")):
+            prob.set_precision(mode)
+            for _ in range(args.warmup):
+                step()
+            c_ms, c_its, c_rels = timed(args.steps)
+            c_dev = sum(c_ms)
+            compare.append({"precision": label, "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT,
+                            "ms_per_step": c_dev / args.steps, "iterations_per_solve": sum(c_its) / len(c_its),
+                            "rel_kkt_residual": max(c_rels), "speedup_time_to_solve": dev_ms / c_dev})
         prob.set_precision(0)
-        c_dev = sum(c_ms)
-        compare = {"precision": "mixed (FP32 preconditioner, FP64 residual/dots/updates)",
-                   "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT, "ms_per_step": c_dev / args.steps,
-                   "iterations_per_solve": sum(c_its) / len(c_its), "rel_kkt_residual": max(c_rels),
-                   "speedup_time_to_solve": dev_ms / c_dev}
 
     # ---- end to end: host (pinned) inputs in, host outputs back, per step
     xh = np.empty((g.T + 1, g.nodes, g.n))
@@ -499,7 +505,7 @@ def run_ours(args, dist):
             "rel_kkt_residual": max(rels),
             "wall_ms": (w1 - w0) * 1e3,
             "roofline": roofline,
-            "compare_mixed": compare,
+            "compare_precision": compare,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk,
@@ -508,8 +514,72 @@ def run_ours(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args, dist):
+    """Batched workload: `args.batch` uneven instances solved by one graph
+    launch, against the same instances solved one after another."""
+    import torch
+
+    from paper_2304_04980_gb300 import lq2d
+
+    lq2d.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    grids = synth.batch_grids(args.batch)
+    probs = [lq2d.Problem.from_grid(gr) for gr in grids]
+    if args.precision != "fp64":
+        for p in probs:
+            p.set_precision(1 if args.precision == "mixed" else 2)
+    batch = lq2d.Batch(probs)
+    unknowns = sum(gr.nodes * (gr.T + 1) * gr.n for gr in grids)
+    for _ in range(args.warmup):
+        batch.solve(args.tol, 2, 2, 100000, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    its = 0
+    launches0 = sum(p.stats()["launches_total"] for p in probs)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        out = batch.solve(args.tol, 2, 2, 100000, stream=stream)
+        ev[k][1].record(stream)
+        its += sum(out["iterations"])
+    torch.cuda.synchronize()
+    b_ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches = sum(p.stats()["launches_total"] for p in probs) - launches0
+    # the same instances one after another (one graph launch each)
+    for p in probs[:4]:
+        p.solve_device(args.tol, 2, 2, 100000, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s_its = 0
+    for p in probs:
+        s_its += p.solve_device(args.tol, 2, 2, 100000, stream=stream)["iterations"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_ms = e0.elapsed_time(e1)
+    line = {
+        "metric": "batched time-to-solve at 1e-8 rel KKT residual (instances/s)", "value": args.steps * len(probs) / (b_ms / 1e3),
+        "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": b_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": "batch%d: K, N in 8..64, T in 50..200, n = 4, m = 2, coupling in 0.02..0.2" % len(probs),
+                   "precision": args.precision, "tol": args.tol, "S": 2, "L": 2, "unknowns": unknowns},
+        "pcg_iters_per_s": its / (b_ms / 1e3),
+        "sequential": {"ms_for_all": s_ms, "instances_per_s": len(probs) / (s_ms / 1e3), "iterations": s_its},
+        "speedup_vs_sequential": s_ms / (b_ms / args.steps),
+        "gpu_launches": launches,
+    }
+    batch.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.batch > 0:
+        run_batch(args, Dist())
+        return
     dist = Dist()
     if args.impl == "reference":
         run_reference(args, dist)   # rank 0 only; no process group needed

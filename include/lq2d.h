@@ -69,10 +69,16 @@ enum {
                                 true residual does not (default 3) */
   LQ2D_OPT_PRECONDITIONER = 5, /* 0: NBJM, Algorithm 2 (default); 1: none (plain CG on Delta,
                                   used to estimate kappa(Delta)) */
-  LQ2D_OPT_KAPPA = 6          /* 1: record the PCG coefficients of each solve and estimate the
+  LQ2D_OPT_KAPPA = 6,         /* 1: record the PCG coefficients of each solve and estimate the
                                   extreme eigenvalues of the preconditioned operator (Lanczos
                                   matrix of CG; Section V reports kappa before and after
                                   preconditioning); read them with lq2d_get_stats */
+  LQ2D_OPT_SWEEP_THREADS = 7  /* 128 (default) or 256: threads per CTA of the NBJM sweeps, i.e.
+                                  a tile of 128/g or 256/g time steps per CTA (g = 2n rounded
+                                  up to a power of two); sets the FP64 and FP32 sweeps alike.
+                                  lq2d_autotune picks it by timing. Results may differ in
+                                  the last bits between widths (partial sums are grouped per
+                                  CTA) */
 };
 
 /* Statistics of the last solve on a handle. */
@@ -181,6 +187,20 @@ int lq2d_apply_delta_device(lq2d_problem *h, const void *d_in, void *d_out, void
 int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const void *d_r,
                               void *d_q, void *stream);
 
+/* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS) for this problem's shape
+ * and the handle's current precision mode by timing: runs D_S (S outer x L
+ * inner sweeps, Algorithm 2) once as warm-up and then `reps` times with each
+ * candidate width (128, 256), with CUDA events on `stream`, and keeps the
+ * faster for later solves of this precision mode (FP64 and FP32 sweeps keep
+ * separate choices).  The problem's right-hand side is the input; the
+ * handle's solution buffers are not touched.
+ *   threads (out, may be NULL): the chosen width
+ *   ms      (out, may be NULL): its time per D_S application, milliseconds
+ * Errors: LQ2D_EINVAL for bad S, L or reps < 1; LQ2D_ECUDA (the previous
+ * width is kept).  Returns after the work on `stream` is complete. */
+int lq2d_autotune(lq2d_problem *h, int outer_S, int inner_L, int reps, int *threads, double *ms,
+                  void *stream);
+
 /* y = Delta d as lq2d_apply_delta_device computes it, for callers that may
  * not allocate device memory: it takes the raw problem blocks (device
  * pointers, layouts as in lq2d_create) instead of a handle, and keeps its
@@ -205,18 +225,49 @@ int lq2d_apply_delta_static(int K, int N, int T, int n, int m,
                             const double *d_Q, const double *d_R, const double *d_Q_T,
                             const void *d_in, void *d_out, void *stream);
 
+/* Many problems (uneven K, N, T, each with its own data and x0) solved by
+ * one launch: a CUDA graph with one independent chain per problem (the
+ * initial residual and preconditioner, the device loop of Algorithm 1
+ * under a conditional while node, the recovery of x, u and the KKT
+ * residual), built on the first lq2d_batch_solve and rebuilt only when tol,
+ * S, L, max_iter or a problem's precision/preconditioner/stop options
+ * change.  The problems stay owned by the caller and must outlive the
+ * batch; their data may be replaced with lq2d_update(_device) between
+ * solves without a rebuild.  Results stay in each problem: read them with
+ * lq2d_get_solution_device and lq2d_get_stats. */
+typedef struct lq2d_batch lq2d_batch; /* opaque, library-owned */
+int lq2d_batch_create(lq2d_batch **out, int count, lq2d_problem *const *problems);
+/* iterations [count], rel_kkt_residuals [count] and statuses [count] are
+ * optional outputs; the return value is LQ2D_OK when every problem
+ * converged, else the first failing status.  Returns after the work on
+ * `stream` is complete. */
+int lq2d_batch_solve(lq2d_batch *b, double tol, int outer_S, int inner_L, int max_iter,
+                     int *iterations, double *rel_kkt_residuals, int *statuses, void *stream);
+void lq2d_batch_destroy(lq2d_batch *b);
+/* Copies the solution of the problem's last solve (x, u, costate, layouts as
+ * in lq2d_solve_device) into device buffers; any pointer may be NULL. */
+int lq2d_get_solution_device(lq2d_problem *h, void *d_x, void *d_u, void *d_costate, void *stream);
+
 int lq2d_set_option(lq2d_problem *h, int option, double value);
 int lq2d_get_stats(const lq2d_problem *h, lq2d_stats *out);
 
-/* Precision of the preconditioner (Algorithm 2).
+/* Precision of the preconditioner (Algorithm 2) and of the Delta product.
  *   0: FP64 everywhere (default).
  *   1: the sweeps, the banded factors of Phi_bar and the Omega~/Xi~ blocks in
  *      FP32; the residual, iterate, direction, Delta d, every dot product and
  *      the stop test stay FP64.  The FP32 preconditioner is not exactly
  *      symmetric, so the next direction uses the flexible ratio
  *      q_new'(r_new - r_old) / mu_old.  The tolerance still applies to the
- *      FP64 residual.  Mode 1 allocates FP32 copies of the operands on its
- *      first use and refreshes them at every setup. */
+ *      FP64 residual.
+ *   2: as 1, and the product Delta d inside the Krylov loop in FP32 too.
+ *      The recurrence residual then drifts from the true one at FP32 level,
+ *      so the loop runs in phases: a phase ends when the recurrence
+ *      residual has dropped by 1e4 (or meets the tolerance), the residual is
+ *      recomputed in FP64 from the iterate and the iteration restarts from
+ *      it (reliable residual replacement).  Residual recomputation, the
+ *      direction update and every dot product stay FP64.
+ * Modes 1 and 2 allocate FP32 copies of the operands on first use and
+ * refresh them at every setup. */
 int lq2d_set_precision(lq2d_problem *h, int mode);
 
 /* Frees every device buffer of the handle; NULL is a no-op. */

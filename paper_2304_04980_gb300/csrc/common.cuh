@@ -37,6 +37,8 @@ struct SolverState {
   int hist_cap;       // entries (pairs) available in hist
   unsigned int counters[8];  // arrival counters of the last-block reductions
   double* hist;       // optional: vartheta_j at [2j], beta_j at [2j+1] (Lanczos estimate), or NULL
+  double tol_bound;   // the tolerance itself, in the units of stop_bound
+  double phase_rho2;  // > 0: a phase also ends once ||r||^2 <= phase_rho2 ||r_start||^2 (precision mode 2)
 };
 
 // Records the PCG coefficients of step j (called by the last block of the

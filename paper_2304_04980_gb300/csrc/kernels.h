@@ -8,7 +8,19 @@
 namespace lq2d {
 
 constexpr int kOpThreads = 256;     // threads per block of the node-time kernels
-constexpr int kSweepThreads = 128;  // threads per block of the sweep kernels
+constexpr int kSweepThreads = 128;  // default threads per block of the sweep kernels (128 or 256)
+
+// Operands of the Delta product in its compute precision CT (double, or
+// float in precision mode 2): the grid blocks and the per-node Q^-1, Q_T^-1,
+// B R^-1 B'.
+template <typename CT>
+struct OpData {
+  const CT* Aself;  // [NN][n][n]
+  const CT* Anb;    // [NN][4][n][n]
+  const CT* Qi;     // [NN][n][n]
+  const CT* QTi;    // [NN][n][n]
+  const CT* Sb;     // [NN][n][n]
+};
 
 // Operands of the preconditioner in the precision VT of the sweeps (double,
 // or float in the mixed mode): the banded block-Cholesky factors of
@@ -58,24 +70,34 @@ enum SweepVariant {
 };
 
 struct KernelTable {
-  // z = Q~^-1 A~' dn with dn = q + beta d_old (beta from the state when use_beta);
-  // q is the preconditioner output, double (FP64 mode) or float (mixed mode)
-  void (*delta_z)(const Grid& g, const NodeData& nd, const double* q, const double* dold, double* z,
+  // z = Q~^-1 A~' dn with dn = q + beta d_old (beta from the state when use_beta),
+  // computed in CT; q is the preconditioner output (double, or float in the
+  // mixed modes); z is stored in CT.
+  void (*delta_z)(const Grid& g, const OpData<double>& op, const double* q, const double* dold, double* z,
                   const SolverState* st, int use_beta, cudaStream_t s);
-  void (*delta_z_f32)(const Grid& g, const NodeData& nd, const float* q, const double* dold, double* z,
+  void (*delta_z_f32)(const Grid& g, const OpData<double>& op, const float* q, const double* dold, double* z,
                       const SolverState* st, int use_beta, cudaStream_t s);
+  // precision mode 2: everything in FP32, d_old read from its FP32 copy
+  void (*delta_z_f32op)(const Grid& g, const OpData<float>& op, const float* q, const float* dold32, float* z,
+                        const SolverState* st, int use_beta, cudaStream_t s);
   // y = A~ z + B~ R~^-1 B~' dn; in loop mode also writes dn into dout, reduces
   // y' dn and sets vartheta = mu / (y' dn) (Algorithm 1 lines 7-8)
-  void (*delta_y)(const Grid& g, const NodeData& nd, const double* z, const double* q, const double* dold,
+  void (*delta_y)(const Grid& g, const OpData<double>& op, const double* z, const double* q, const double* dold,
                   double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s);
-  void (*delta_y_f32)(const Grid& g, const NodeData& nd, const double* z, const float* q, const double* dold,
+  void (*delta_y_f32)(const Grid& g, const OpData<double>& op, const double* z, const float* q, const double* dold,
                       double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s);
+  // precision mode 2: also writes the FP32 copy of the new direction
+  void (*delta_y_f32op)(const Grid& g, const OpData<float>& op, const float* z, const float* q, const double* dold,
+                        double* dout, float* dout32, double* y, double* partials, SolverState* st, int loop_mode,
+                        cudaStream_t s);
   // FP64 sweep (Algorithm 2 step); the OmegaMu variant sets beta = mu_new / mu_old
-  void (*sweep)(int variant, const Grid& g, const PrecData<double>& pd, const SweepArgsT<double>& a,
+  // threads: CTA width of the sweep, 128 or 256 (a tile of threads / 2n time
+  // steps, 2n rounded up to a power of two)
+  void (*sweep)(int variant, int threads, const Grid& g, const PrecData<double>& pd, const SweepArgsT<double>& a,
                 SolverState* st, cudaStream_t s);
   // FP32 sweep of the mixed mode; the OmegaMu variant sets the flexible
   // beta = q_new'(r_new - r_old) / mu_old = -vartheta q_new'y / mu_old
-  void (*sweep_f32)(int variant, const Grid& g, const PrecData<float>& pd, const SweepArgsT<float>& a,
+  void (*sweep_f32)(int variant, int threads, const Grid& g, const PrecData<float>& pd, const SweepArgsT<float>& a,
                     SolverState* st, cudaStream_t s);
   // KKT residual pieces and cost of (x, u, delta): out[0] = sum of squared
   // residual entries, out[1] = x'Q~x + u'R~u, out[2] = max |A~x + B~u + omega~|
@@ -89,7 +111,7 @@ const KernelTable* kernel_table(int n);
 
 // dimension-generic helpers (kernels_misc.cu)
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
-                       int keep_iter, double* hist, int hist_cap, cudaStream_t s);
+                       int keep_iter, double* hist, int hist_cap, double phase_rho2, cudaStream_t s);
 // identity preconditioner (plain CG): q = r, mu = r'r; with update, the PCG
 // update of Algorithm 1 lines 9-11 first
 void launch_ident(const Grid& g, bool update, double* r, double* delta, const double* y, const double* d,

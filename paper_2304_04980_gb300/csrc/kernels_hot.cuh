@@ -12,14 +12,14 @@ namespace lq2d {
 namespace hot {
 
 // A_hat block in row p, column "p's neighbour in direction dir".
-template <int NS>
-__device__ __forceinline__ const double* ahat_row(const NodeData& nd, int p, int dir) {
+template <int NS, typename D>
+__device__ __forceinline__ auto ahat_row(const D& nd, int p, int dir) {
   return dir == kSelf ? nd.Aself + (size_t)p * NS * NS : nd.Anb + ((size_t)p * 4 + (dir - 1)) * NS * NS;
 }
 
 // A_hat block in row r, column p, for r = neighbour of p in direction dir.
-template <int NS>
-__device__ __forceinline__ const double* ahat_col(const NodeData& nd, int r, int dir) {
+template <int NS, typename D>
+__device__ __forceinline__ auto ahat_col(const D& nd, int r, int dir) {
   const int slot = dir == kWest ? 1 : dir == kEast ? 0 : dir == kNorth ? 3 : 2;  // F, E, H, G of r
   return dir == kSelf ? nd.Aself + (size_t)r * NS * NS : nd.Anb + ((size_t)r * 4 + slot) * NS * NS;
 }
@@ -31,10 +31,10 @@ __device__ __forceinline__ const double* ahat_col(const NodeData& nd, int r, int
 // dn = q + beta d_old is formed on the fly (Algorithm 1 line 14 fused into
 // line 7); beta comes from the device state.
 // ---------------------------------------------------------------------------
-template <int NS, typename QT>
-__global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd, const QT* __restrict__ q,
-                                                             const double* __restrict__ dold,
-                                                             double* __restrict__ z,
+template <int NS, typename QT, typename CT, typename DT>
+__global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> nd, const QT* __restrict__ q,
+                                                             const DT* __restrict__ dold,
+                                                             CT* __restrict__ z,
                                                              const SolverState* __restrict__ st, int use_beta) {
   if (use_beta && st->done) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,27 +42,30 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd
   const int Tp = g.T + 1;
   const int p = (int)(idx / Tp), t = (int)(idx % Tp);
   const int i = p / g.N, j = p % g.N;
-  const double beta = use_beta ? st->beta : 0.0;
-  const bool mix = beta != 0.0;
-  double w[NS];
+  // dn = q + beta d_old is formed in the precision of d_old (FP64, or FP32
+  // when the FP32 copy of d is read)
+  const DT beta = use_beta ? (DT)st->beta : DT(0);
+  const bool mix = beta != DT(0);
+  CT w[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    double dv = (double)q[k * g.Ps + idx];
+    DT dv = (DT)q[k * g.Ps + idx];
     if (mix) dv += beta * dold[k * g.Ps + idx];
-    w[k] = -dv;
+    w[k] = (CT)(-dv);
   }
   if (t < g.T) {
 #pragma unroll
     for (int dir = 0; dir < 5; ++dir) {
       const int r = nbr_node(i, j, dir, g.K, g.N);
       if (r < 0) continue;
-      const double* blk = ahat_col<NS>(nd, r, dir);
+      const CT* blk = ahat_col<NS>(nd, r, dir);
       const long long ridx = (long long)r * Tp + t + 1;
-      double dv[NS];
+      CT dv[NS];
 #pragma unroll
       for (int c = 0; c < NS; ++c) {
-        dv[c] = (double)q[c * g.Ps + ridx];
-        if (mix) dv[c] += beta * dold[c * g.Ps + ridx];
+        DT dd = (DT)q[c * g.Ps + ridx];
+        if (mix) dd += beta * dold[c * g.Ps + ridx];
+        dv[c] = (CT)dd;
       }
 #pragma unroll
       for (int c = 0; c < NS; ++c)
@@ -70,10 +73,10 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd
         for (int k = 0; k < NS; ++k) w[k] += blk[c * NS + k] * dv[c];
     }
   }
-  const double* Qb = (t == g.T ? nd.QTi : nd.Qi) + (size_t)p * NS * NS;
+  const CT* Qb = (t == g.T ? nd.QTi : nd.Qi) + (size_t)p * NS * NS;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    double s = 0.0;
+    CT s = CT(0);
 #pragma unroll
     for (int c = 0; c < NS; ++c) s += Qb[k * NS + c] * w[c];
     z[k * g.Ps + idx] = s;
@@ -86,12 +89,13 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, NodeData nd
 // Loop mode (Algorithm 1 lines 7-8, 14): dn = q + beta d_old is written back
 // to d (each thread owns its entry), y' dn is reduced and vartheta set.
 // ---------------------------------------------------------------------------
-template <int NS, bool LOOP, typename QT>
-__global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd, const double* __restrict__ z,
+template <int NS, bool LOOP, typename QT, typename CT>
+__global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> nd, const CT* __restrict__ z,
                                                              const QT* __restrict__ q,
                                                              const double* __restrict__ dold,
-                                                             double* __restrict__ dout, double* __restrict__ y,
-                                                             double* __restrict__ partials, SolverState* st) {
+                                                             double* __restrict__ dout, float* __restrict__ dout32,
+                                                             double* __restrict__ y, double* __restrict__ partials,
+                                                             SolverState* st) {
   if (LOOP && st->done) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
@@ -100,7 +104,8 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd
     const int p = (int)(idx / Tp), t = (int)(idx % Tp);
     const int i = p / g.N, j = p % g.N;
     const double beta = LOOP ? st->beta : 0.0;
-    double dn[NS], yk[NS];
+    double dn[NS];
+    CT yk[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       double dv = (double)q[k * g.Ps + idx];
@@ -113,9 +118,9 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd
       for (int dir = 0; dir < 5; ++dir) {
         const int r = nbr_node(i, j, dir, g.K, g.N);
         if (r < 0) continue;
-        const double* blk = ahat_row<NS>(nd, p, dir);
+        const CT* blk = ahat_row<NS>(nd, p, dir);
         const long long ridx = (long long)r * Tp + t - 1;
-        double zv[NS];
+        CT zv[NS];
 #pragma unroll
         for (int c = 0; c < NS; ++c) zv[c] = z[c * g.Ps + ridx];
 #pragma unroll
@@ -123,18 +128,19 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, NodeData nd
 #pragma unroll
           for (int c = 0; c < NS; ++c) yk[k] += blk[k * NS + c] * zv[c];
       }
-      const double* S = nd.Sb + (size_t)p * NS * NS;
+      const CT* S = nd.Sb + (size_t)p * NS * NS;
 #pragma unroll
       for (int k = 0; k < NS; ++k)
 #pragma unroll
-        for (int c = 0; c < NS; ++c) yk[k] += S[k * NS + c] * dn[c];
+        for (int c = 0; c < NS; ++c) yk[k] += S[k * NS + c] * (CT)dn[c];
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      y[k * g.Ps + idx] = yk[k];
+      y[k * g.Ps + idx] = (double)yk[k];
       if (LOOP) {
         dout[k * g.Ps + idx] = dn[k];
-        acc += yk[k] * dn[k];
+        if (dout32 != nullptr) dout32[k * g.Ps + idx] = (float)dn[k];
+        acc += (double)yk[k] * dn[k];
       }
     }
   }
@@ -253,68 +259,82 @@ __global__ void __launch_bounds__(kOpThreads) kkt_kernel(Grid g, NodeData nd, co
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int NS, typename QT>
-void launch_delta_z(const Grid& g, const NodeData& nd, const QT* q, const double* dold, double* z,
+template <int NS, typename QT, typename CT, typename DT>
+void launch_delta_z(const Grid& g, const OpData<CT>& op, const QT* q, const DT* dold, CT* z,
                     const SolverState* st, int use_beta, cudaStream_t s) {
   const long long blocks = (g.P + kOpThreads - 1) / kOpThreads;
-  delta_z_kernel<NS, QT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, q, dold, z, st, use_beta);
+  delta_z_kernel<NS, QT, CT, DT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, op, q, dold, z, st, use_beta);
 }
 
-template <int NS, typename QT>
-void launch_delta_y(const Grid& g, const NodeData& nd, const double* z, const QT* q, const double* dold,
-                    double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s) {
+template <int NS, typename QT, typename CT>
+void launch_delta_y_impl(const Grid& g, const OpData<CT>& op, const CT* z, const QT* q, const double* dold,
+                         double* dout, float* dout32, double* y, double* partials, SolverState* st, int loop_mode,
+                         cudaStream_t s) {
   const long long blocks = (g.P + kOpThreads - 1) / kOpThreads;
   if (loop_mode)
-    delta_y_kernel<NS, true, QT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, z, q, dold, dout, y, partials, st);
+    delta_y_kernel<NS, true, QT, CT>
+        <<<(unsigned)blocks, kOpThreads, 0, s>>>(g, op, z, q, dold, dout, dout32, y, partials, st);
   else
-    delta_y_kernel<NS, false, QT><<<(unsigned)blocks, kOpThreads, 0, s>>>(g, nd, z, q, dold, dout, y, partials, st);
+    delta_y_kernel<NS, false, QT, CT>
+        <<<(unsigned)blocks, kOpThreads, 0, s>>>(g, op, z, q, dold, dout, dout32, y, partials, st);
 }
 
-template <int NS, typename VT>
-void launch_sweep(int variant, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a, SolverState* st,
-                  cudaStream_t s) {
-  const unsigned blocks = sweep_blocks<NS>(g);
-  const size_t shm = sweep_smem_bytes<NS, VT>();
+template <int NS, typename QT, typename CT>
+void launch_delta_y(const Grid& g, const OpData<CT>& op, const CT* z, const QT* q, const double* dold,
+                    double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s) {
+  launch_delta_y_impl<NS, QT, CT>(g, op, z, q, dold, dout, nullptr, y, partials, st, loop_mode, s);
+}
+
+template <int NS, typename VT, int THR>
+void launch_sweep_t(int variant, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a, SolverState* st,
+                    cudaStream_t s) {
+  const unsigned blocks = sweep_blocks<NS, THR>(g);
+  const size_t shm = sweep_smem_bytes<NS, VT, THR>();
   switch (variant) {
-    case kSweepPlain: nbjm_sweep_kernel<NS, kSweepPlain, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st); break;
-    case kSweepUpdate:
-      nbjm_sweep_kernel<NS, kSweepUpdate, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st);
-      break;
-    case kSweepOmega: nbjm_sweep_kernel<NS, kSweepOmega, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st); break;
-    case kSweepOmegaMu:
-      nbjm_sweep_kernel<NS, kSweepOmegaMu, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st);
-      break;
-    case kSweepXiOmega:
-      nbjm_sweep_kernel<NS, kSweepXiOmega, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st);
-      break;
-    default: nbjm_sweep_kernel<NS, kSweepXi, VT><<<blocks, kSweepThreads, shm, s>>>(g, pd, a, st); break;
+    case kSweepPlain: nbjm_sweep_kernel<NS, kSweepPlain, VT, THR><<<blocks, THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepUpdate: nbjm_sweep_kernel<NS, kSweepUpdate, VT, THR><<<blocks, THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepOmega: nbjm_sweep_kernel<NS, kSweepOmega, VT, THR><<<blocks, THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepOmegaMu: nbjm_sweep_kernel<NS, kSweepOmegaMu, VT, THR><<<blocks, THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepXiOmega: nbjm_sweep_kernel<NS, kSweepXiOmega, VT, THR><<<blocks, THR, shm, s>>>(g, pd, a, st); break;
+    default: nbjm_sweep_kernel<NS, kSweepXi, VT, THR><<<blocks, THR, shm, s>>>(g, pd, a, st); break;
   }
+}
+
+// Sweep launch with the CTA width (threads) chosen for the problem: 128 or
+// 256 threads, i.e. a tile of 128/GS or 256/GS time steps per CTA.
+template <int NS, typename VT>
+void launch_sweep(int variant, int threads, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a,
+                  SolverState* st, cudaStream_t s) {
+  if (threads == 256) launch_sweep_t<NS, VT, 256>(variant, g, pd, a, st, s);
+  else launch_sweep_t<NS, VT, 128>(variant, g, pd, a, st, s);
 }
 
 // Allows every sweep instantiation its shared-memory footprint (above the
 // 48 KB default for n >= 8 in FP64); called once per device before use.
-template <int NS, typename VT>
+template <int NS, typename VT, int THR>
 cudaError_t prepare_sweeps_t() {
-  const int shm = (int)sweep_smem_bytes<NS, VT>();
+  const int shm = (int)sweep_smem_bytes<NS, VT, THR>();
   cudaError_t e = cudaSuccess;
   auto set = [&](const void* f) {
     cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
     if (r != cudaSuccess) e = r;
   };
-  set((const void*)nbjm_sweep_kernel<NS, kSweepPlain, VT>);
-  set((const void*)nbjm_sweep_kernel<NS, kSweepUpdate, VT>);
-  set((const void*)nbjm_sweep_kernel<NS, kSweepOmega, VT>);
-  set((const void*)nbjm_sweep_kernel<NS, kSweepOmegaMu, VT>);
-  set((const void*)nbjm_sweep_kernel<NS, kSweepXi, VT>);
-  set((const void*)nbjm_sweep_kernel<NS, kSweepXiOmega, VT>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepPlain, VT, THR>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepUpdate, VT, THR>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepOmega, VT, THR>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepOmegaMu, VT, THR>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepXi, VT, THR>);
+  set((const void*)nbjm_sweep_kernel<NS, kSweepXiOmega, VT, THR>);
   return e;
 }
 
 template <int NS>
 cudaError_t prepare_sweeps() {
-  cudaError_t e = prepare_sweeps_t<NS, double>();
-  cudaError_t f = prepare_sweeps_t<NS, float>();
-  return e != cudaSuccess ? e : f;
+  cudaError_t e[4] = {prepare_sweeps_t<NS, double, 128>(), prepare_sweeps_t<NS, float, 128>(),
+                      prepare_sweeps_t<NS, double, 256>(), prepare_sweeps_t<NS, float, 256>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 
 template <int NS>
@@ -326,8 +346,11 @@ void launch_kkt(const Grid& g, const NodeData& nd, const double* x, const double
 
 template <int NS>
 const KernelTable* make_table() {
-  static const KernelTable t = {&launch_delta_z<NS, double>, &launch_delta_z<NS, float>,
-                                &launch_delta_y<NS, double>, &launch_delta_y<NS, float>,
+  static const KernelTable t = {&launch_delta_z<NS, double, double, double>,
+                                &launch_delta_z<NS, float, double, double>,
+                                &launch_delta_z<NS, float, float, float>,
+                                &launch_delta_y<NS, double, double>, &launch_delta_y<NS, float, double>,
+                                &launch_delta_y_impl<NS, float, float>,
                                 &launch_sweep<NS, double>,   &launch_sweep<NS, float>,
                                 &launch_kkt<NS>, &prepare_sweeps<NS>};
   return &t;

@@ -31,7 +31,7 @@ const KernelTable* kernel_table(int n) {
 namespace {
 
 __global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
-                                  int keep_iter, double* hist, int hist_cap) {
+                                  int keep_iter, double* hist, int hist_cap, double phase_rho2) {
   st->mu = 0.0;
   st->beta = 0.0;
   st->ydot = 0.0;
@@ -39,6 +39,8 @@ __global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int
   st->bnorm2 = *bnorm2;
   st->stop_mode = stop_mode;
   st->stop_bound = stop_mode == 0 ? tol * tol * st->bnorm2 : tol;
+  st->tol_bound = st->stop_bound;
+  st->phase_rho2 = stop_mode == 0 ? phase_rho2 : 0.0;
   if (!keep_iter) st->iter = 0;
   st->max_iter = max_iter;
   st->done = 0;
@@ -148,7 +150,10 @@ __global__ void init_residual_kernel(Grid g, const double* __restrict__ rhs, con
   if (grid_reduce2<true>(s2, mx, partials, &st->counters[kCntInit], &t0, &t1)) {
     st->rnorm2 = t0;
     st->rnorm_inf = t1;
-    const bool pass = st->stop_mode == 0 ? (t0 <= st->stop_bound) : (t1 < st->stop_bound);
+    const bool pass = st->stop_mode == 0 ? (t0 <= st->tol_bound) : (t1 < st->tol_bound);
+    // a phase of precision mode 2 ends once the recurrence residual has
+    // dropped by sqrt(phase_rho2) (or meets the tolerance)
+    if (st->phase_rho2 > 0.0) st->stop_bound = fmax(st->tol_bound, st->phase_rho2 * t0);
     if (!isfinite(t0)) st->done = kBreakdown;
     else if (pass) st->done = kConverged;
     else if (st->iter >= st->max_iter) st->done = kMaxIter;
@@ -251,8 +256,8 @@ inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + th
 }  // namespace
 
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
-                       int keep_iter, double* hist, int hist_cap, cudaStream_t s) {
-  init_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, stop_mode, bnorm2, keep_iter, hist, hist_cap);
+                       int keep_iter, double* hist, int hist_cap, double phase_rho2, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(st, tol, max_iter, stop_mode, bnorm2, keep_iter, hist, hist_cap, phase_rho2);
 }
 
 void launch_ident(const Grid& g, bool update, double* r, double* delta, const double* y, const double* d,

@@ -31,13 +31,18 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 struct GraphEntry {
-  int S = 0, L = 0, precision = 0, precond = 0;
+  int S = 0, L = 0, precision = 0, precond = 0, threads = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
 constexpr int kMaxGraphs = 8;
 constexpr int kHistCap = 1 << 16;  // PCG steps whose coefficients are kept for the Lanczos estimate
+// Precision mode 2: a phase of the FP32-product Krylov loop ends once the
+// recurrence residual has dropped by kPhaseRho; the FP64 true residual then
+// replaces it (at most kPhaseRestarts times).
+constexpr double kPhaseRho = 1e-4;
+constexpr int kPhaseRestarts = 40;
 constexpr int kStreamChunk = 4;  // steps enqueued between stop-flag reads (driver 1)
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
@@ -81,15 +86,37 @@ struct lq2d_problem {
   int precision = 0;
   PrecData<double> pd64{};
   PrecData<float> pd32{};
+  OpData<double> op64{};
+  OpData<float> op32{};
   float* f32_buf = nullptr;  // FP32 copies of the factors and node blocks (mode 1, allocated on first use)
+  float* d32 = nullptr;      // FP32 copy of the direction d (mode 2)
   int precond_kind = 0;      // 0: NBJM (Algorithm 2), 1: none (plain CG)
+  int sweep_threads[2] = {kSweepThreads, kSweepThreads};  // CTA width of the FP64 / FP32 sweeps (128 or 256)
   int kappa = 0;             // record the PCG coefficients and estimate the condition number
   double* hist = nullptr;    // device: vartheta_j, beta_j pairs
   std::vector<double> h_hist;
   int graph_body_kernels = 0;  // kernels per device-loop body of the last graph launch (0: no graph)
 };
 
+// Many problems solved by one graph launch: one independent chain per
+// problem (initial residual and preconditioner, the device loop of
+// Algorithm 1 under a conditional while node, recovery), all in one graph.
+struct lq2d_batch {
+  std::vector<lq2d_problem*> probs;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double* results = nullptr;   // device: kBatchSlot doubles per problem
+  double* h_results = nullptr; // pinned host mirror
+  // what the graph was built for
+  double tol = 0.0;
+  int S = 0, L = 0, max_iter = -1;
+  std::vector<int> built_modes;
+};
+
 namespace {
+
+constexpr int kBatchSlot = 32;  // doubles per problem in the batch result array
 
 int dev_alloc(lq2d_problem* h, double** p, size_t count) {
   void* ptr = nullptr;
@@ -181,7 +208,7 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   ALLOC(h->stage_u, (size_t)g.Pu * m);
   // partials: two values per block, two reductions in the KKT kernel
   const long long op_blocks = (g.P + kOpThreads - 1) / kOpThreads;
-  const long long sw_blocks = ((long long)g.V * (T + 1) * 32 + kSweepThreads - 1) / kSweepThreads;
+  const long long sw_blocks = (long long)g.V * (T + 1);  // at least one time step per sweep CTA
   const long long pblocks = op_blocks > sw_blocks ? op_blocks : sw_blocks;
   ALLOC(h->partials, (size_t)pblocks * 4 + 64);
   double* misc = nullptr;
@@ -202,11 +229,15 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   nd.Qi = sb.Qi; nd.QTi = sb.QTi; nd.Sb = sb.Sb; nd.RiBt = sb.RiBt; nd.Om = sb.Om; nd.AQ = sb.AQ;
   nd.QAt = sb.QAt; nd.fac = sb.fac; nd.fac_rec = fac_rec; nd.fac_vc = fac_vc;
   h->pd64 = PrecData<double>{sb.fac, fac_rec, fac_vc, sb.Om, sb.AQ, sb.QAt, sb.Qm};
+  h->op64 = OpData<double>{sb.Aself, sb.Anb, sb.Qi, sb.QTi, sb.Sb};
   return LQ2D_OK;
 }
 
-// Element counts of the preconditioner operands: factors, Omega~, AQ, QAt, Q.
-void prec_counts(const lq2d_problem* h, long long c[5]) {
+// Element counts of the FP32 operand copies: the preconditioner's factors,
+// Omega~, AQ, QAt, Q, then the Delta product's A, E/F/G/H, Q^-1, Q_T^-1,
+// B R^-1 B'.
+constexpr int kF32Arrays = 10;
+void prec_counts(const lq2d_problem* h, long long c[kF32Arrays]) {
   const Grid& g = h->g;
   const long long nn = (long long)g.n * g.n;
   c[0] = (long long)g.V * 2 * h->nd.fac_vc;
@@ -214,19 +245,25 @@ void prec_counts(const lq2d_problem* h, long long c[5]) {
   c[2] = c[1];
   c[3] = c[1];
   c[4] = (long long)g.NN * nn;
+  c[5] = (long long)g.NN * nn;
+  c[6] = (long long)g.NN * 4 * nn;
+  c[7] = c[5];
+  c[8] = c[5];
+  c[9] = c[5];
 }
 
-// FP32 copies of the preconditioner operands for the mixed mode.
+// FP32 copies of the operands for the mixed modes.
 void convert_prec_f32(lq2d_problem* h, cudaStream_t s) {
-  long long c[5];
+  long long c[kF32Arrays];
   prec_counts(h, c);
-  const double* src[5] = {h->sb.fac, h->sb.Om, h->sb.AQ, h->sb.QAt, h->sb.Qm};
+  const double* src[kF32Arrays] = {h->sb.fac, h->sb.Om, h->sb.AQ, h->sb.QAt, h->sb.Qm,
+                                   h->sb.Aself, h->sb.Anb, h->sb.Qi, h->sb.QTi, h->sb.Sb};
   float* dst = h->f32_buf;
-  for (int a = 0; a < 5; ++a) {
+  for (int a = 0; a < kF32Arrays; ++a) {
     launch_to_f32(src[a], dst, c[a], s);
     dst += c[a];
   }
-  h->launches += 5;
+  h->launches += kF32Arrays;
 }
 
 // Setup on `s`: inverses, splitting blocks, factors, right-hand side and its
@@ -328,9 +365,9 @@ const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, b
         cudaEventRecord(e0, s);
       }
       if constexpr (sizeof(VT) == 4)
-        h->kt->sweep_f32(variant, h->g, h->pd32, a, st, s);
+        h->kt->sweep_f32(variant, h->sweep_threads[1], h->g, h->pd32, a, st, s);
       else
-        h->kt->sweep(variant, h->g, h->pd64, a, st, s);
+        h->kt->sweep(variant, h->sweep_threads[0], h->g, h->pd64, a, st, s);
       h->launches += 1;
       if (timing) cudaEventRecord(e1, s);
       prev = bufs[out_i];
@@ -342,13 +379,13 @@ const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, b
 
 const void* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
                             const double* r_in, cudaStream_t s, bool timing) {
-  if (h->precision == 1) return enqueue_precond_t<float>(h, S, L, fuse_update, mu, st, r_in, s, timing);
+  if (h->precision >= 1) return enqueue_precond_t<float>(h, S, L, fuse_update, mu, st, r_in, s, timing);
   return enqueue_precond_t<double>(h, S, L, fuse_update, mu, st, r_in, s, timing);
 }
 
 // The preconditioner output q is FP32 only for the NBJM preconditioner in
 // the mixed mode; the identity preconditioner copies r in FP64.
-bool q_is_f32(const lq2d_problem* h) { return h->precision == 1 && h->precond_kind == 0; }
+bool q_is_f32(const lq2d_problem* h) { return h->precision >= 1 && h->precond_kind == 0; }
 
 // y = Delta dn with dn = q + beta d_old; q is the preconditioner output in
 // the preconditioner's precision.
@@ -365,14 +402,21 @@ void enqueue_delta(lq2d_problem* h, const void* q, const double* dold, double* d
     e1 = h->ev_pool[k + 1];
     cudaEventRecord(e0, s);
   }
-  if (q_is_f32(h)) {
+  if (q_is_f32(h) && h->precision == 2 && loop) {
+    // precision mode 2: the product inside the Krylov loop in FP32; the
+    // first kernel reads the FP32 copy of d, the second writes both copies
     const float* qf = static_cast<const float*>(q);
-    h->kt->delta_z_f32(h->g, h->nd, qf, dold, h->z, st, loop ? 1 : 0, s);
-    h->kt->delta_y_f32(h->g, h->nd, h->z, qf, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+    float* zf = reinterpret_cast<float*>(h->z);
+    h->kt->delta_z_f32op(h->g, h->op32, qf, h->d32, zf, st, 1, s);
+    h->kt->delta_y_f32op(h->g, h->op32, zf, qf, dold, dout, h->d32, y, h->partials, st, 1, s);
+  } else if (q_is_f32(h)) {
+    const float* qf = static_cast<const float*>(q);
+    h->kt->delta_z_f32(h->g, h->op64, qf, dold, h->z, st, loop ? 1 : 0, s);
+    h->kt->delta_y_f32(h->g, h->op64, h->z, qf, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
   } else {
     const double* qd = static_cast<const double*>(q);
-    h->kt->delta_z(h->g, h->nd, qd, dold, h->z, st, loop ? 1 : 0, s);
-    h->kt->delta_y(h->g, h->nd, h->z, qd, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
+    h->kt->delta_z(h->g, h->op64, qd, dold, h->z, st, loop ? 1 : 0, s);
+    h->kt->delta_y(h->g, h->op64, h->z, qd, dold, dout, y, h->partials, st, loop ? 1 : 0, s);
   }
   h->launches += 2;
   if (timing) cudaEventRecord(e1, s);
@@ -401,12 +445,15 @@ void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
   enqueue_precond(h, S, L, true, true, h->st, h->r, s, timing);
 }
 
+// CTA width of the sweeps the current precision mode launches.
+int current_threads(const lq2d_problem* h) { return h->sweep_threads[h->precision >= 1 ? 1 : 0]; }
+
 int sweeps_per_step(const lq2d_problem* h, int S, int L) { return h->precond_kind == 1 ? 1 : S * L; }
 
 int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   for (int i = 0; i < h->ngraphs; ++i)
     if (h->graphs[i].S == S && h->graphs[i].L == L && h->graphs[i].precision == h->precision &&
-        h->graphs[i].precond == h->precond_kind) {
+        h->graphs[i].precond == h->precond_kind && h->graphs[i].threads == current_threads(h)) {
       *exec = h->graphs[i].exec;
       return LQ2D_OK;
     }
@@ -421,6 +468,7 @@ int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   ge.L = L;
   ge.precision = h->precision;
   ge.precond = h->precond_kind;
+  ge.threads = current_threads(h);
   LQ_CUDA(cudaGraphCreate(&ge.graph, 0));
   cudaGraphConditionalHandle hc;
   LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, ge.graph, 1u, cudaGraphCondAssignDefault));
@@ -599,13 +647,16 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     int rc = dev_alloc(h, &h->hist, 2 * (size_t)kHistCap);
     if (rc) return rc;
   }
-  launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, h->kappa ? h->hist : nullptr, kHistCap, s);
+  const double phase_rho2 = h->precision == 2 ? kPhaseRho * kPhaseRho : 0.0;
+  const int max_restarts = h->precision == 2 ? std::max(h->max_restarts, kPhaseRestarts) : h->max_restarts;
+  launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, h->kappa ? h->hist : nullptr, kHistCap,
+                    phase_rho2, s);
   h->launches += 2;  // state and initial residual
   if (d_delta0) {
     h->launches += 3;
     launch_to_internal(d_delta0, h->thA, g.NN, g.T + 1, g.n, g.Ps, s);
-    kt->delta_z(g, h->nd, h->thA, nullptr, h->z, nullptr, 0, s);
-    kt->delta_y(g, h->nd, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
+    kt->delta_z(g, h->op64, h->thA, nullptr, h->z, nullptr, 0, s);
+    kt->delta_y(g, h->op64, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
     launch_init_residual(g, h->rhs, h->y, h->r, h->delta, h->thA, h->partials, h->st, s);
   } else {
     launch_init_residual(g, h->rhs, nullptr, h->r, h->delta, nullptr, h->partials, h->st, s);
@@ -628,7 +679,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     h->launches += 3;  // recovery
     // recovery (Section II-B): x = Q~^-1 A~' delta into z, u = R~^-1 B~' delta,
     // and the full KKT residual of (x, u, delta)
-    kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
+    kt->delta_z(g, h->op64, h->delta, nullptr, h->z, nullptr, 0, s);
     launch_recover_u(g, h->nd, h->delta, h->u, s);
     kt->kkt(g, h->nd, h->z, h->u, h->delta, h->rhs, h->partials, h->st, h->kkt_out, s);
     LQ_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
@@ -642,14 +693,14 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     const double bn = std::sqrt(hs.bnorm2);
     rel = bn > 0 ? std::sqrt(h->h_kkt[0]) / bn : std::sqrt(h->h_kkt[0]);
     const bool true_pass = h->stop_mode == 0 ? (rel <= tol || h->h_kkt[0] == 0.0) : (h->h_kkt[2] < tol);
-    if (hs.done == kConverged && !true_pass && restarts < h->max_restarts && hs.iter < max_iter) {
+    if (hs.done == kConverged && !true_pass && restarts < max_restarts && hs.iter < max_iter) {
       // the recurrence residual passed but the true one did not: restart
       // from the current iterate with r = r_delta - Delta delta
       ++restarts;
       h->launches += 4;
-      launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 1, nullptr, 0, s);
-      kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
-      kt->delta_y(g, h->nd, h->z, h->delta, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
+      launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 1, nullptr, 0, phase_rho2, s);
+      kt->delta_z(g, h->op64, h->delta, nullptr, h->z, nullptr, 0, s);
+      kt->delta_y(g, h->op64, h->z, h->delta, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
       launch_init_residual(g, h->rhs, h->y, h->r, h->delta, h->delta, h->partials, h->st, s);
       continue;
     }
@@ -736,9 +787,9 @@ void enqueue_nbjm_outer(lq2d_problem* h, int L, int step, cudaStream_t s) {
       a.theta_in = prev;
     }
     if constexpr (sizeof(VT) == 4)
-      h->kt->sweep_f32(variant, h->g, h->pd32, a, h->st, s);
+      h->kt->sweep_f32(variant, h->sweep_threads[1], h->g, h->pd32, a, h->st, s);
     else
-      h->kt->sweep(variant, h->g, h->pd64, a, h->st, s);
+      h->kt->sweep(variant, h->sweep_threads[0], h->g, h->pd64, a, h->st, s);
     prev = B[others[l & 1]];
   }
   launch_nbjm_diff(h->g, prev, cur < 0 ? nullptr : B[cur], sizeof(VT) == 4, h->partials, h->st, s);
@@ -751,9 +802,9 @@ int solve_nbjm_impl(lq2d_problem* h, double eps, int L, int max_outer, double* d
   if (L < 1) return fail(LQ2D_EINVAL, "inner_L must be >= 1");
   if (max_outer < 1) return fail(LQ2D_EINVAL, "max_outer must be >= 1");
   const Grid& g = h->g;
-  const bool f32 = h->precision == 1;
+  const bool f32 = h->precision >= 1;
   std::memset(&h->stats, 0, sizeof(h->stats));
-  launch_init_state(h->st, eps, max_outer, 1, h->bnorm, 0, nullptr, 0, s);
+  launch_init_state(h->st, eps, max_outer, 1, h->bnorm, 0, nullptr, 0, 0.0, s);
   h->launches += 1;
   cudaEvent_t flag_ev[2];
   LQ_CUDA(cudaEventCreateWithFlags(&flag_ev[0], cudaEventDisableTiming));
@@ -791,7 +842,7 @@ int solve_nbjm_impl(lq2d_problem* h, double eps, int L, int max_outer, double* d
     LQ_CUDA(cudaMemsetAsync(h->delta, 0, (size_t)g.Ps * g.n * sizeof(double), s));
   }
   // recovery (Section II-B) and the true KKT residual of the result
-  h->kt->delta_z(g, h->nd, h->delta, nullptr, h->z, nullptr, 0, s);
+  h->kt->delta_z(g, h->op64, h->delta, nullptr, h->z, nullptr, 0, s);
   launch_recover_u(g, h->nd, h->delta, h->u, s);
   h->kt->kkt(g, h->nd, h->z, h->u, h->delta, h->rhs, h->partials, h->st, h->kkt_out, s);
   h->launches += 3 + (f32 ? 1 : 0);
@@ -815,6 +866,91 @@ int solve_nbjm_impl(lq2d_problem* h, double eps, int L, int max_outer, double* d
   h->stats.status = status;
   if (status == LQ2D_ENOCONV) return fail(status, "max_outer reached before the exit test passed");
   if (status == LQ2D_EBREAKDOWN) return fail(status, "non-finite iterate");
+  return LQ2D_OK;
+}
+
+// The part of a solve before the device loop: state, r^(0) = r_delta,
+// q = P^-1 r^(0) with mu, d = 0 (Algorithm 1 lines 1-5).
+void enqueue_solve_init(lq2d_problem* h, double tol, int S, int L, int max_iter, cudaStream_t s) {
+  const Grid& g = h->g;
+  const double phase_rho2 = h->precision == 2 ? kPhaseRho * kPhaseRho : 0.0;
+  launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, nullptr, 0, phase_rho2, s);
+  launch_init_residual(g, h->rhs, nullptr, h->r, h->delta, nullptr, h->partials, h->st, s);
+  if (h->precond_kind == 1) launch_ident(g, false, h->r, h->delta, h->y, h->d, h->thB, h->partials, h->st, s);
+  else enqueue_precond(h, S, L, false, true, h->st, h->r, s, false);
+  cudaMemsetAsync(h->d, 0, (size_t)g.Ps * g.n * sizeof(double), s);
+}
+
+// Recovery (Section II-B) and the copy of the state and KKT figures into
+// the batch result slot.
+void enqueue_solve_finish(lq2d_problem* h, double* slot, cudaStream_t s) {
+  const Grid& g = h->g;
+  h->kt->delta_z(g, h->op64, h->delta, nullptr, h->z, nullptr, 0, s);
+  launch_recover_u(g, h->nd, h->delta, h->u, s);
+  h->kt->kkt(g, h->nd, h->z, h->u, h->delta, h->rhs, h->partials, h->st, h->kkt_out, s);
+  cudaMemcpyAsync(slot, h->st, sizeof(SolverState), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(slot + 24, h->kkt_out, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+// The per-problem settings a captured batch graph depends on.
+int batch_mode_key(const lq2d_problem* h) {
+  return ((current_threads(h) * 4 + h->precision) * 4 + h->precond_kind) * 4 + h->stop_mode;
+}
+
+int batch_build(lq2d_batch* b, double tol, int S, int L, int max_iter) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  static_assert(sizeof(SolverState) <= 24 * sizeof(double), "batch slot");
+  cudaGraph_t root;
+  LQ_CUDA(cudaGraphCreate(&root, 0));
+  b->graph = root;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  for (size_t i = 0; i < b->probs.size(); ++i) {
+    lq2d_problem* h = b->probs[i];
+    // initial part, appended to the root graph with no dependency
+    LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, root, nullptr, nullptr, 0, mode));
+    const long long before = h->launches;
+    enqueue_solve_init(h, tol, S, L, max_iter, b->cap);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    LQ_CUDA(cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+    cudaGraph_t captured = nullptr;
+    LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+    // the device loop under a conditional while node
+    cudaGraphConditionalHandle hc;
+    LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, root, 1u, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_storage, 0, sizeof(cp_storage));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    LQ_CUDA(cudaGraphAddNode(&cnode, root, tail.data(), nullptr, tail.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, mode));
+    enqueue_step(h, S, L, b->cap, false);
+    launch_loop_ctrl(h->st, hc, b->cap);
+    LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+    // recovery after the loop
+    LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, root, &cnode, nullptr, 1, mode));
+    enqueue_solve_finish(h, b->results + i * kBatchSlot, b->cap);
+    LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+    h->launches = before;  // captured, not launched: counted per batch solve
+  }
+  cudaError_t e = cudaGraphInstantiate(&b->exec, root, 0);
+  if (e != cudaSuccess) return fail(LQ2D_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+  b->tol = tol;
+  b->S = S;
+  b->L = L;
+  b->max_iter = max_iter;
+  b->built_modes.clear();
+  for (lq2d_problem* h : b->probs) b->built_modes.push_back(batch_mode_key(h));
   return LQ2D_OK;
 }
 
@@ -947,8 +1083,8 @@ int lq2d_apply_delta_device(lq2d_problem* h, const void* d_in, void* d_out, void
   const Grid& g = h->g;
   h->launches += 4;
   launch_to_internal(static_cast<const double*>(d_in), h->thA, g.NN, g.T + 1, g.n, g.Ps, s);
-  h->kt->delta_z(g, h->nd, h->thA, nullptr, h->z, nullptr, 0, s);
-  h->kt->delta_y(g, h->nd, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
+  h->kt->delta_z(g, h->op64, h->thA, nullptr, h->z, nullptr, 0, s);
+  h->kt->delta_y(g, h->op64, h->z, h->thA, nullptr, nullptr, h->y, h->partials, nullptr, 0, s);
   launch_to_api(h->y, static_cast<double*>(d_out), g.NN, g.T + 1, g.n, g.Ps, s);
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
@@ -965,7 +1101,7 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
   launch_to_internal(static_cast<const double*>(d_r), h->y, g.NN, g.T + 1, g.n, g.Ps, s);
   const void* q = enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
   const double* qd = static_cast<const double*>(q);
-  if (h->precision == 1) {
+  if (h->precision >= 1) {
     // widen the FP32 result into thA (free after the sweeps) before the layout change
     launch_to_f64(static_cast<const float*>(q), h->thA, (long long)g.Ps * g.n, s);
     h->launches += 1;
@@ -977,12 +1113,158 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
   return LQ2D_OK;
 }
 
+int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double* ms, void* stream) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  if (S < 1) return fail(LQ2D_EINVAL, "outer_S must be >= 1");
+  if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2");
+  if (reps < 1) return fail(LQ2D_EINVAL, "reps must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Grid& g = h->g;
+  const int slot = h->precision >= 1 ? 1 : 0;
+  const int saved = h->sweep_threads[slot];
+  // the right-hand side of the problem stands in for a residual
+  LQ_CUDA(cudaMemcpyAsync(h->y, h->rhs, (size_t)g.Ps * g.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t e0, e1;
+  LQ_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(LQ2D_ECUDA, "cudaEventCreate failed");
+  }
+  const int cand[2] = {128, 256};
+  double best_ms = 0.0;
+  int best = saved;
+  cudaError_t err = cudaSuccess;
+  for (int c = 0; c < 2 && err == cudaSuccess; ++c) {
+    h->sweep_threads[slot] = cand[c];
+    enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
+    cudaEventRecord(e1, s);
+    err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    const double per = (double)t / reps;
+    if (err == cudaSuccess && (c == 0 || per < best_ms)) {
+      best_ms = per;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    h->sweep_threads[slot] = saved;
+    return fail(LQ2D_ECUDA, cudaGetErrorString(err));
+  }
+  h->sweep_threads[slot] = best;
+  if (threads) *threads = best;
+  if (ms) *ms = best_ms;
+  return LQ2D_OK;
+}
+
 int lq2d_solve_nbjm_device(lq2d_problem* h, double eps, int inner_L, int max_outer, void* d_x, void* d_u,
                            void* d_costate, int* outer_iterations, double* rel_kkt_residual, void* stream) {
   if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
   return solve_nbjm_impl(h, eps, inner_L, max_outer, static_cast<double*>(d_x), static_cast<double*>(d_u),
                          static_cast<double*>(d_costate), outer_iterations, rel_kkt_residual,
                          static_cast<cudaStream_t>(stream));
+}
+
+int lq2d_batch_create(lq2d_batch** out, int count, lq2d_problem* const* problems) {
+  if (!out || count < 1 || !problems) return fail(LQ2D_EINVAL, "batch needs a positive count and a problem array");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!problems[i]) return fail(LQ2D_EINVAL, "null problem in batch");
+  lq2d_batch* b = new lq2d_batch();
+  b->probs.assign(problems, problems + count);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->results, (size_t)count * kBatchSlot * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_results, (size_t)count * kBatchSlot * sizeof(double));
+  if (e != cudaSuccess) {
+    lq2d_batch_destroy(b);
+    return fail(e == cudaErrorMemoryAllocation ? LQ2D_ENOMEM : LQ2D_ECUDA, cudaGetErrorString(e));
+  }
+  *out = b;
+  return LQ2D_OK;
+}
+
+int lq2d_batch_solve(lq2d_batch* b, double tol, int S, int L, int max_iter, int* iterations, double* rel_kkt,
+                     int* statuses, void* stream) {
+  if (!b) return fail(LQ2D_EINVAL, "batch is NULL");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(LQ2D_EINVAL, "tol must be positive and finite");
+  if (S < 1 || L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "outer_S >= 1 and even inner_L >= 2 required");
+  if (max_iter < 0) return fail(LQ2D_EINVAL, "max_iter must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool rebuild = !b->exec || b->tol != tol || b->S != S || b->L != L || b->max_iter != max_iter;
+  for (size_t i = 0; !rebuild && i < b->probs.size(); ++i) {
+    const lq2d_problem* h = b->probs[i];
+    rebuild = b->built_modes[i] != batch_mode_key(h);
+  }
+  if (rebuild) {
+    int rc = batch_build(b, tol, S, L, max_iter);
+    if (rc) return rc;
+  }
+  const size_t count = b->probs.size();
+  LQ_CUDA(cudaGraphLaunch(b->exec, s));
+  LQ_CUDA(cudaMemcpyAsync(b->h_results, b->results, count * kBatchSlot * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  int worst = LQ2D_OK;
+  for (size_t i = 0; i < count; ++i) {
+    lq2d_problem* h = b->probs[i];
+    const SolverState& hs = *reinterpret_cast<const SolverState*>(b->h_results + i * kBatchSlot);
+    const double* kkt = b->h_results + i * kBatchSlot + 24;
+    const double bn = std::sqrt(hs.bnorm2);
+    const double rel = bn > 0 ? std::sqrt(kkt[0]) / bn : std::sqrt(kkt[0]);
+    const bool true_pass = h->stop_mode == 0 ? (rel <= tol || kkt[0] == 0.0) : (kkt[2] < tol);
+    int status;
+    switch (hs.done) {
+      case kConverged: status = true_pass ? LQ2D_OK : LQ2D_ENOCONV; break;
+      case kMaxIter: status = LQ2D_ENOCONV; break;
+      case kBreakdown: status = LQ2D_EBREAKDOWN; break;
+      case kLoopCap: status = LQ2D_ETIMEOUT; break;
+      default: status = LQ2D_ECUDA; break;
+    }
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    h->stats.iterations = hs.iter;
+    h->stats.rel_residual = bn > 0 ? std::sqrt(hs.rnorm2) / bn : std::sqrt(hs.rnorm2);
+    h->stats.rel_kkt_residual = rel;
+    h->stats.kkt_inf = kkt[2];
+    h->stats.cost = 0.5 * kkt[1];
+    h->stats.status = status;
+    h->stats.body_executions = hs.body_count;
+    const int sweeps = sweeps_per_step(h, S, L);
+    h->launches += (2 + sweeps) + 3 + (long long)hs.body_count * (2 + sweeps + 1);
+    if (iterations) iterations[i] = hs.iter;
+    if (rel_kkt) rel_kkt[i] = rel;
+    if (statuses) statuses[i] = status;
+    if (status != LQ2D_OK && worst == LQ2D_OK) worst = status;
+  }
+  if (worst != LQ2D_OK) return fail(worst, "some problems of the batch did not converge; see statuses");
+  return LQ2D_OK;
+}
+
+void lq2d_batch_destroy(lq2d_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->results) cudaFree(b->results);
+  if (b->h_results) cudaFreeHost(b->h_results);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+int lq2d_get_solution_device(lq2d_problem* h, void* d_x, void* d_u, void* d_costate, void* stream) {
+  if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Grid& g = h->g;
+  if (d_x) launch_to_api(h->z, static_cast<double*>(d_x), g.NN, g.T + 1, g.n, g.Ps, s);
+  if (d_u) launch_to_api(h->u, static_cast<double*>(d_u), g.NN, g.T, g.m, g.Pus, s);
+  if (d_costate) launch_to_api(h->delta, static_cast<double*>(d_costate), g.NN, g.T + 1, g.n, g.Ps, s);
+  h->launches += (d_x != nullptr) + (d_u != nullptr) + (d_costate != nullptr);
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  return LQ2D_OK;
 }
 
 int lq2d_set_option(lq2d_problem* h, int option, double value) {
@@ -1011,6 +1293,10 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
       if (v < 0) return fail(LQ2D_EINVAL, "max restarts must be >= 0");
       h->max_restarts = v;
       return LQ2D_OK;
+    case LQ2D_OPT_SWEEP_THREADS:
+      if (v != 128 && v != 256) return fail(LQ2D_EINVAL, "sweep threads must be 128 or 256");
+      h->sweep_threads[0] = h->sweep_threads[1] = v;
+      return LQ2D_OK;
     default:
       return fail(LQ2D_EINVAL, "unknown option");
   }
@@ -1025,11 +1311,20 @@ int lq2d_get_stats(const lq2d_problem* h, lq2d_stats* out) {
 
 int lq2d_set_precision(lq2d_problem* h, int mode) {
   if (!h) return fail(LQ2D_EINVAL, "handle is NULL");
-  if (mode != 0 && mode != 1) return fail(LQ2D_EINVAL, "precision mode must be 0 (FP64) or 1 (FP32 preconditioner)");
-  if (mode == 1 && !h->f32_buf) {
-    long long c[5];
+  if (mode < 0 || mode > 2)
+    return fail(LQ2D_EINVAL, "precision mode must be 0 (FP64), 1 (FP32 preconditioner) or 2 (FP32 preconditioner and product)");
+  if (mode == 2 && !h->d32) {
+    double* buf = nullptr;
+    int rc = dev_alloc(h, &buf, ((size_t)h->g.Ps * h->g.n + 1) / 2 + 64);
+    if (rc) return rc;
+    h->d32 = reinterpret_cast<float*>(buf);
+    LQ_CUDA(cudaMemset(h->d32, 0, (size_t)h->g.Ps * h->g.n * sizeof(float)));
+  }
+  if (mode >= 1 && !h->f32_buf) {
+    long long c[kF32Arrays];
     prec_counts(h, c);
-    const long long total = c[0] + c[1] + c[2] + c[3] + c[4];
+    long long total = 0;
+    for (int a = 0; a < kF32Arrays; ++a) total += c[a];
     double* buf = nullptr;
     int rc = dev_alloc(h, &buf, (size_t)(total + 1) / 2 + 64);
     if (rc) return rc;
@@ -1044,6 +1339,16 @@ int lq2d_set_precision(lq2d_problem* h, int mode) {
     h->pd32.QAt = p;
     p += c[3];
     h->pd32.Qm = p;
+    p += c[4];
+    h->op32.Aself = p;
+    p += c[5];
+    h->op32.Anb = p;
+    p += c[6];
+    h->op32.Qi = p;
+    p += c[7];
+    h->op32.QTi = p;
+    p += c[8];
+    h->op32.Sb = p;
     h->pd32.fac_rec = h->nd.fac_rec;
     h->pd32.fac_vc = h->nd.fac_vc;
     convert_prec_f32(h, nullptr);

@@ -6,11 +6,12 @@
 // consecutive time steps; a group of GS lanes solves one (v, t) block, lane
 // a owning unknown a = jj*NS + k of every pair-row (node (i, 2v+jj),
 // component k).  All groups of a CTA walk the K pair-rows together.  For
-// pair-row i+1 the CTA copies into shared memory, with cp.async while
-// pair-row i is computed:
-//   * the factor blocks of pair-row i+1 (both time classes when the tile
+// pair-row i+2 the CTA copies into shared memory, with cp.async while
+// pair-row i is computed (three buffers):
+//   * the factor blocks of pair-row i+2 (both time classes when the tile
 //     holds t = T), read by every group of the tile;
-//   * the right-hand side of the pair-row's two nodes for the TT steps;
+//   * the pair-row's own entries for the TT steps (the right-hand side, or
+//     r, y, d, delta in the sweep that performs the PCG update);
 //   * the eight neighbouring nodes' theta (Omega~ term, same t) or
 //     delta^(s) (Xi~ term, t-1 and t+1) for the TT steps: contiguous runs
 //     in the component-plane layout;
@@ -18,23 +19,30 @@
 // Per pair-row i:
 //   forward:  y_i = L0_i^-1 (tau_i - L1_i y_{i-1} - L2_i y_{i-2})
 //   backward: x_i = L0_i^-T (y_i - L1_{i+1}' x_{i+1} - L2_{i+2}' x_{i+2})
-// y is kept in theta_out between the two passes.  At t = 0, Phi_bar = Q^-1
-// node by node, so theta = Q tau.
+// Each lane computes one row of every block product; the forward pass reads
+// the row-major blocks and the backward pass the transposed ones, so a
+// lane's operands are contiguous in shared memory.  The group exchanges its
+// 2n values of w and y through shared memory.  y is kept in theta_out
+// between the two passes.  At t = 0, Phi_bar = Q^-1 node by node, so
+// theta = Q tau.
 #pragma once
+
+#include <string.h>
 
 #include "kernels.h"
 
 namespace lq2d {
 namespace hot {
 
-template <int NS>
+template <int NS, int THR>
 struct SweepGeom {
   static constexpr int G2 = 2 * NS;
   static constexpr int GS = G2 <= 2 ? 2 : G2 <= 4 ? 4 : G2 <= 8 ? 8 : G2 <= 16 ? 16 : 32;
   static constexpr int BS = G2 * G2;
-  static constexpr int TT = kSweepThreads / GS;  // time steps per CTA
+  static constexpr int TT = THR / GS;            // time steps per CTA
   static constexpr int NH = 8;                   // staged neighbour nodes per pair-row
   static constexpr int HW = TT + 2;              // staged time window (t0-1 .. t0+TT)
+  static constexpr int NB = 3;                   // pipeline depth (buffers)
 };
 
 __device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
@@ -58,36 +66,47 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// The eight staged neighbours of pair-row i of column pair v (j0 = 2v).
+// CNT consecutive elements from shared memory, with 16-byte loads when a run
+// of CNT elements is a multiple of 16 bytes (callers keep runs 16-byte
+// aligned in that case).
+template <typename VT, int CNT>
+__device__ __forceinline__ void lds_run(const VT* p, VT (&out)[CNT]) {
+  constexpr int bytes = CNT * (int)sizeof(VT);
+  if constexpr (bytes % 16 == 0) {
+    const int4* q = reinterpret_cast<const int4*>(p);
+#pragma unroll
+    for (int e = 0; e < bytes / 16; ++e) {
+      const int4 v = q[e];
+      memcpy(&out[e * (16 / (int)sizeof(VT))], &v, 16);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < CNT; ++e) out[e] = p[e];
+  }
+}
+
+// Offsets (di, dj) of the eight staged neighbours of pair-row i of column
+// pair v (j0 = 2v), packed as two bits of di + 1 and three bits of dj + 2.
 // Omega~ (off-pair, same t):  (i,j0-1) (i-1,j0-1) (i+1,j0-1) (i,j0-2)
 //                             (i,j0+2) (i-1,j0+2) (i+1,j0+2) (i,j0+3)
 // Xi~ (5-point, t -/+ 1):     (i,j0) (i,j0+1) (i-1,j0) (i+1,j0)
 //                             (i-1,j0+1) (i+1,j0+1) (i,j0-1) (i,j0+2)
+constexpr unsigned long long pack_offsets(const int (&di)[8], const int (&dj)[8]) {
+  unsigned long long r = 0;
+  for (int h = 0; h < 8; ++h)
+    r |= (unsigned long long)(((di[h] + 1) & 3) | (((dj[h] + 2) & 7) << 2)) << (5 * h);
+  return r;
+}
+constexpr int kOmDi[8] = {0, -1, 1, 0, 0, -1, 1, 0};
+constexpr int kOmDj[8] = {-1, -1, -1, -2, 2, 2, 2, 3};
+constexpr int kXiDi[8] = {0, 0, -1, 1, -1, 1, 0, 0};
+constexpr int kXiDj[8] = {0, 1, 0, 0, 1, 1, -1, 2};
+constexpr unsigned long long kOmPacked = pack_offsets(kOmDi, kOmDj);
+constexpr unsigned long long kXiPacked = pack_offsets(kXiDi, kXiDj);
+
 __device__ __forceinline__ int staged_node(bool xi, int h, int i, int j0, int K, int N) {
-  int di = 0, dj = 0;
-  if (!xi) {
-    switch (h) {
-      case 0: dj = -1; break;
-      case 1: di = -1; dj = -1; break;
-      case 2: di = 1; dj = -1; break;
-      case 3: dj = -2; break;
-      case 4: dj = 2; break;
-      case 5: di = -1; dj = 2; break;
-      case 6: di = 1; dj = 2; break;
-      default: dj = 3; break;
-    }
-  } else {
-    switch (h) {
-      case 0: break;
-      case 1: dj = 1; break;
-      case 2: di = -1; break;
-      case 3: di = 1; break;
-      case 4: di = -1; dj = 1; break;
-      case 5: di = 1; dj = 1; break;
-      case 6: dj = -1; break;
-      default: dj = 2; break;
-    }
-  }
+  const unsigned long long code = ((xi ? kXiPacked : kOmPacked) >> (5 * h)) & 31ull;
+  const int di = (int)(code & 3) - 1, dj = (int)(code >> 2) - 2;
   const int ii = i + di, jj = j0 + dj;
   if (ii < 0 || ii >= K || jj < 0 || jj >= N) return -1;
   return ii * N + jj;
@@ -96,26 +115,28 @@ __device__ __forceinline__ int staged_node(bool xi, int h, int i, int j0, int K,
 // Index of the staged node for off-pair neighbour o of column jj (order o0..o4
 // of offpair_node), and for direction dir (self, west, east, north, south)
 // of the 5-point stencil.
-__device__ __forceinline__ int h_of_offpair(int jj, int o) {
-  return jj == 0 ? o : (o == 4 ? 0 : o + 4);
-}
+__device__ __forceinline__ int h_of_offpair(int jj, int o) { return jj == 0 ? o : (o == 4 ? 0 : o + 4); }
 __device__ __forceinline__ int h_of_dir(int jj, int dir) {
   if (jj == 0) return dir == 0 ? 0 : dir == 1 ? 6 : dir == 2 ? 1 : dir == 3 ? 2 : 3;
   return dir == 0 ? 1 : dir == 1 ? 0 : dir == 2 ? 7 : dir == 3 ? 4 : 5;
 }
 
-template <int NS, typename VT>
+template <int NS, typename VT, int THR>
 struct SweepSmem {
-  using Geo = SweepGeom<NS>;
-  VT fac[2][2][3 * Geo::BS];                  // [buffer][class][3 blocks]
-  double src[2][2][NS][Geo::TT];              // [buffer][jj][k][t]
-  VT halo[2][Geo::NH][NS][Geo::HW];           // [buffer][h][k][t window]
-  VT blk[2][2][10][NS * NS];                  // [buffer][jj][block][n x n]
+  using Geo = SweepGeom<NS, THR>;
+  static constexpr int NB = Geo::NB;
+  VT fac[NB][2][3 * Geo::BS];         // [buffer][class][3 blocks]
+  VT halo[NB][Geo::NH][Geo::HW][NS];  // [buffer][h][t window][k]
+  VT blk[NB][2][10][NS * NS];         // [buffer][jj][block][n x n]
+  VT xw[Geo::TT][Geo::G2];            // per group: w of the current pair-row
+  VT xy[Geo::TT][Geo::G2];            // per group: y or x of the current pair-row
+  double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]
+  unsigned valid[NB];                 // [buffer] bit h: staged neighbour h inside the grid
 };
 
-template <int NS, int VAR, typename VT>
-__global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
-                                                                   SolverState* st) {
+template <int NS, int VAR, typename VT, int THR>
+__global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
+                                                         SolverState* st) {
   // VT = float is the mixed mode: FP32 factors, blocks and iterates, with
   // the flexible (Polak-Ribiere) ratio for the next direction
   constexpr bool FLEX = sizeof(VT) == 4;
@@ -124,10 +145,10 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
   constexpr bool OMEGA = VAR == kSweepOmega || VAR == kSweepOmegaMu || VAR == kSweepXiOmega;
   constexpr bool MU = VAR == kSweepOmegaMu;
   constexpr bool HALO = XI || OMEGA;
-  using Geo = SweepGeom<NS>;
+  using Geo = SweepGeom<NS, THR>;
   constexpr int G2 = Geo::G2, GS = Geo::GS, BS = Geo::BS, TT = Geo::TT, HW = Geo::HW;
   extern __shared__ __align__(16) unsigned char sweep_smem[];
-  SweepSmem<NS, VT>& sm = *reinterpret_cast<SweepSmem<NS, VT>*>(sweep_smem);
+  SweepSmem<NS, VT, THR>& sm = *reinterpret_cast<SweepSmem<NS, VT, THR>*>(sweep_smem);
 
   if (st != nullptr && st->done) return;
   const int Tp = g.T + 1;
@@ -144,50 +165,51 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
   const unsigned gmask = GS == 32 ? 0xffffffffu : (((1u << GS) - 1u) << (lane32 & ~(GS - 1)));
   const int t = t0 + grp;
   const bool active = t <= g.T;
-  const int ac = al < G2 ? al : 0;
+  const bool lane_ok = al < G2;
+  const int ac = lane_ok ? al : 0;
   const int jj = ac / NS, k = ac % NS;
   const int j = j0 + jj;
-  const bool node_ok = active && al < G2 && j < g.N;
+  const bool node_ok = active && lane_ok && j < g.N;
   const long long kP = (long long)k * g.Ps;
   const int cls = (t == g.T) ? 1 : 0;
+  const int my_slot = has_last ? cls : 0;  // tiles without t = T stage class 0 only, at slot 0
   const double vth = UPDATE ? st->theta : 0.0;
   const bool flex_dot = FLEX && MU && st->have_mu;
   const VT* fac_pair = pd.fac + (size_t)(2 * v) * pd.fac_vc;  // class c at fac_pair + c * fac_vc
+  const int ncls = has_last ? 2 : 1;
+  constexpr int CH = 16 / sizeof(VT);  // elements per 16-byte copy
   double acc0 = 0.0, acc1 = 0.0;
 
   // ---- staging of the forward step for pair-row i into buffer b
   auto stage_forward = [&](int i, int b) {
-    // factor blocks L2', L1', L0^-1' of pair-row i, per class in the tile
-    const int ncls = has_last ? 2 : 1;
-    constexpr int CH = 16 / sizeof(VT);  // elements per 16-byte copy
-    for (int e = tid * CH; e < ncls * 3 * BS; e += kSweepThreads * CH) {
-      const int c = e / (3 * BS), off = e % (3 * BS);  // slot c holds class c
-      cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + off);
+    // row-major L2, L1, L0^-1 (record blocks 3..5) of pair-row i, per class
+    for (int e = tid * CH; e < ncls * 3 * BS; e += THR * CH) {
+      const int c = e / (3 * BS), off = e % (3 * BS);
+      cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + 3 * BS + off);
     }
-    // right-hand side of the pair-row's nodes
-    if (!UPDATE) {
-      for (int e = tid; e < 2 * NS * TT; e += kSweepThreads) {
-        const int cjj = e / (NS * TT), kk = (e / TT) % NS, gg = e % TT;
+    {
+      // the pair-row's own entries: r, y, d, delta (update sweep) or src
+      constexpr int nv = UPDATE ? 4 : 1;
+      for (int e = tid; e < nv * 2 * NS * TT; e += THR) {
+        const int vv = e / (2 * NS * TT), cjj = (e / (NS * TT)) % 2, kk = (e / TT) % NS, gg = e % TT;
         const int tt = t0 + gg;
-        if (tt <= g.T && (cjj == 0 || two_cols)) {
-          const int p = i * g.N + j0 + cjj;
-          cp_async_8(&sm.src[b][cjj][kk][gg], a.src + kk * g.Ps + (long long)p * Tp + tt);
-        }
+        if (tt > g.T || (cjj == 1 && !two_cols)) continue;
+        const double* base = UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src;
+        cp_async_8(&sm.src[b][vv][cjj][kk][gg], base + kk * g.Ps + (long long)(i * g.N + j0 + cjj) * Tp + tt);
       }
     }
     if (HALO) {
       const VT* vec = XI ? a.delta_s : a.theta_in;
-      for (int e = tid; e < Geo::NH * NS * HW; e += kSweepThreads) {
+      for (int e = tid; e < Geo::NH * NS * HW; e += THR) {
         const int h = e / (NS * HW), kk = (e / HW) % NS, w = e % HW;
         const int tt = t0 - 1 + w;
         if (tt < 0 || tt > g.T) continue;
         const int q = staged_node(XI, h, i, j0, g.K, g.N);
         if (q < 0) continue;
-        cp_async_elem(&sm.halo[b][h][kk][w], vec + kk * g.Ps + (long long)q * Tp + tt);
+        cp_async_elem(&sm.halo[b][h][w][kk], vec + kk * g.Ps + (long long)q * Tp + tt);
       }
-      // node blocks: Omega~ (5 per node) or AQ, QAt (5 + 5 per node)
       constexpr int nb = XI ? 10 : 5;
-      for (int e = tid; e < 2 * nb * NS * NS; e += kSweepThreads) {
+      for (int e = tid; e < 2 * nb * NS * NS; e += THR) {
         const int cjj = e / (nb * NS * NS), bb = (e / (NS * NS)) % nb, rc = e % (NS * NS);
         if (cjj == 1 && !two_cols) continue;
         const int p = i * g.N + j0 + cjj;
@@ -196,83 +218,76 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
         else srcb = pd.Om + ((size_t)p * 5 + bb) * NS * NS + rc;
         cp_async_elem(&sm.blk[b][cjj][bb][rc], srcb);
       }
+      if (tid == 0) {
+        unsigned m = 0;
+        for (int h = 0; h < Geo::NH; ++h) m |= (staged_node(XI, h, i, j0, g.K, g.N) >= 0 ? 1u : 0u) << h;
+        sm.valid[b] = m;
+      }
     }
   };
 
-  // ---- staging of the backward step for pair-row i: L0^-1 of i, L1 of i+1,
-  // L2 of i+2 (blocks 5, 4, 3 of their records)
+  // ---- staging of the backward step for pair-row i: the transposed L0^-1
+  // of i, L1 of i+1 and L2 of i+2 (record blocks 2, 1, 0)
   auto stage_backward = [&](int i, int b) {
-    const int ncls = has_last ? 2 : 1;
-    constexpr int CH = 16 / sizeof(VT);
-    for (int e = tid * CH; e < ncls * 3 * BS; e += kSweepThreads * CH) {
+    for (int e = tid * CH; e < ncls * 3 * BS; e += THR * CH) {
       const int c = e / (3 * BS), off = e % (3 * BS);
-      const int part = off / BS, in = off % BS;  // 0: L0^-1 of i, 1: L1 of i+1, 2: L2 of i+2
+      const int part = off / BS, in = off % BS;
       const int row = i + part;
       if (row >= g.K) continue;
-      cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)row * pd.fac_rec + (5 - part) * BS + in);
+      cp_async_16(&sm.fac[b][c][off],
+                  fac_pair + (size_t)c * pd.fac_vc + (size_t)row * pd.fac_rec + (2 - part) * BS + in);
     }
   };
 
   VT ym1[G2], ym2[G2];
 #pragma unroll
-  for (int b = 0; b < G2; ++b) { ym1[b] = VT(0); ym2[b] = VT(0); }
-  // in a tile without t = T only class 0 is staged, at slot 0
-  const int my_slot = has_last ? cls : 0;
+  for (int bb = 0; bb < G2; ++bb) { ym1[bb] = VT(0); ym2[bb] = VT(0); }
 
-  // the update sweep's own entries of r, y, d, delta, loaded one pair-row ahead
-  double nr = 0.0, ny = 0.0, nd_ = 0.0, ndl = 0.0;
-  if (UPDATE && node_ok) {
-    const long long o0 = kP + (long long)j * Tp + t;
-    nr = a.r[o0];
-    ny = a.y[o0];
-    nd_ = a.d[o0];
-    ndl = a.delta[o0];
-  }
+  constexpr int NB = Geo::NB;
   stage_forward(0, 0);
   cp_async_commit();
+  if (g.K > 1) stage_forward(1, 1);
+  cp_async_commit();
   for (int i = 0; i < g.K; ++i) {
-    const int b = i & 1;
-    if (i + 1 < g.K) stage_forward(i + 1, b ^ 1);
+    const int b = i % NB;
+    if (i + 2 < g.K) stage_forward(i + 2, (i + 2) % NB);
     cp_async_commit();
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
-    const double cr = nr, cy = ny, cd = nd_, cdl = ndl;
-    if (UPDATE && node_ok && i + 1 < g.K) {
-      const long long o1 = off + (long long)g.N * Tp;
-      nr = a.r[kP + o1];
-      ny = a.y[kP + o1];
-      nd_ = a.d[kP + o1];
-      ndl = a.delta[kP + o1];
-    }
-    cp_async_wait<1>();
+    cp_async_wait<2>();
     __syncthreads();
+    const unsigned valid = HALO ? sm.valid[b] : 0u;
     VT tau = VT(0);
     if (node_ok) {
       if (UPDATE) {
-        const double rr = cr - vth * cy;
+        const double rr = sm.src[b][0][jj][k][grp] - vth * sm.src[b][1][jj][k][grp];
         a.r[kP + off] = rr;
-        a.delta[kP + off] = cdl + vth * cd;
+        a.delta[kP + off] = sm.src[b][3][jj][k][grp] + vth * sm.src[b][2][jj][k][grp];
         tau = (VT)rr;
         acc0 += rr * rr;
         acc1 = fmax(acc1, fabs(rr));
       } else {
-        tau = (VT)sm.src[b][jj][k][grp];
+        tau = (VT)sm.src[b][0][jj][k][grp];
       }
       if (XI) {
         // (Xi~ delta)_t = A_hat Q^-1 delta_{t-1} + Q^-1 A_hat' delta_{t+1}
 #pragma unroll
         for (int dir = 0; dir < 5; ++dir) {
-          if (nbr_node(i, j, dir, g.K, g.N) < 0) continue;
           const int h = h_of_dir(jj, dir);
+          if (!((valid >> h) & 1u)) continue;
           if (t >= 1) {
-            const VT* blk = &sm.blk[b][jj][dir][k * NS];
+            VT row[NS], hv[NS];
+            lds_run<VT, NS>(&sm.blk[b][jj][dir][k * NS], row);
+            lds_run<VT, NS>(&sm.halo[b][h][grp][0], hv);
 #pragma unroll
-            for (int c = 0; c < NS; ++c) tau += blk[c] * sm.halo[b][h][c][grp];
+            for (int c = 0; c < NS; ++c) tau += row[c] * hv[c];
           }
           if (t < g.T) {
-            const VT* blk = &sm.blk[b][jj][5 + dir][k * NS];
+            VT row[NS], hv[NS];
+            lds_run<VT, NS>(&sm.blk[b][jj][5 + dir][k * NS], row);
+            lds_run<VT, NS>(&sm.halo[b][h][grp + 2][0], hv);
 #pragma unroll
-            for (int c = 0; c < NS; ++c) tau += blk[c] * sm.halo[b][h][c][grp + 2];
+            for (int c = 0; c < NS; ++c) tau += row[c] * hv[c];
           }
         }
         a.rtheta_out[kP + off] = (double)tau;
@@ -293,11 +308,13 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
         } else {
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
-            if (offpair_node(i, j, o, g.K, g.N) < 0) continue;
             const int h = h_of_offpair(jj, o);
-            const VT* blk = &sm.blk[b][jj][o][k * NS];
+            if (!((valid >> h) & 1u)) continue;
+            VT row[NS], hv[NS];
+            lds_run<VT, NS>(&sm.blk[b][jj][o][k * NS], row);
+            lds_run<VT, NS>(&sm.halo[b][h][grp + 1][0], hv);
 #pragma unroll
-            for (int c = 0; c < NS; ++c) tau += blk[c] * sm.halo[b][h][c][grp + 1];
+            for (int c = 0; c < NS; ++c) tau += row[c] * hv[c];
           }
         }
       }
@@ -317,27 +334,36 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
         if (flex_dot) acc1 += (double)out * a.y[kP + off];
       }
     } else {
-      const VT* rec = sm.fac[b][my_slot];
+      const VT* rec = sm.fac[b][my_slot];  // [L2][L1][L0^-1], row-major
       VT w = tau;
       if (i >= 1) {
+        VT row[G2];
+        lds_run<VT, G2>(rec + BS + ac * G2, row);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= rec[BS + bb * G2 + ac] * ym1[bb];
+        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * ym1[bb];
       }
       if (i >= 2) {
+        VT row[G2];
+        lds_run<VT, G2>(rec + ac * G2, row);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= rec[bb * G2 + ac] * ym2[bb];
+        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * ym2[bb];
       }
+      if (lane_ok) sm.xw[grp][al] = w;
+      __syncwarp(gmask);
+      VT wall[G2], row[G2];
+      lds_run<VT, G2>(&sm.xw[grp][0], wall);
+      lds_run<VT, G2>(rec + 2 * BS + ac * G2, row);
       VT yv = VT(0);
 #pragma unroll
-      for (int bb = 0; bb < G2; ++bb) yv += rec[2 * BS + bb * G2 + ac] * __shfl_sync(gmask, w, bb, GS);
+      for (int bb = 0; bb < G2; ++bb) yv += row[bb] * wall[bb];
       if (node_ok) a.theta_out[kP + off] = yv;
+      if (lane_ok) sm.xy[grp][al] = yv;
+      __syncwarp(gmask);
 #pragma unroll
-      for (int bb = 0; bb < G2; ++bb) {
-        ym2[bb] = ym1[bb];
-        ym1[bb] = __shfl_sync(gmask, yv, bb, GS);
-      }
+      for (int bb = 0; bb < G2; ++bb) ym2[bb] = ym1[bb];
+      lds_run<VT, G2>(&sm.xy[grp][0], ym1);
     }
-    __syncthreads();  // buffer b is refilled two steps later
+    __syncthreads();  // buffer b is refilled NB - 2 steps later
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -348,38 +374,57 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
   for (int bb = 0; bb < G2; ++bb) { xp1[bb] = VT(0); xp2[bb] = VT(0); }
   stage_backward(g.K - 1, 0);
   cp_async_commit();
+  if (g.K > 1) stage_backward(g.K - 2, 1);
+  cp_async_commit();
   for (int i = g.K - 1; i >= 0; --i) {
-    const int b = (g.K - 1 - i) & 1;
-    if (i >= 1) stage_backward(i - 1, b ^ 1);
+    const int step = g.K - 1 - i;
+    const int b = step % NB;
+    if (i >= 2) stage_backward(i - 2, (step + 2) % NB);
     cp_async_commit();
-    cp_async_wait<1>();
+    const int p = i * g.N + j;
+    const long long off = node_ok ? (long long)p * Tp + t : 0;
+    VT yown = VT(0);
+    double r_own = 0.0, y_own = 0.0;
+    if (t >= 1 && node_ok) {
+      yown = a.theta_out[kP + off];
+      if (MU) r_own = a.r[kP + off];
+      if (flex_dot) y_own = a.y[kP + off];
+    }
+    cp_async_wait<2>();
     __syncthreads();
     if (t >= 1) {
-      const int p = i * g.N + j;
-      const long long off = node_ok ? (long long)p * Tp + t : 0;
-      const VT* rec = sm.fac[b][my_slot];
-      VT w = node_ok ? a.theta_out[kP + off] : VT(0);
+      const VT* rec = sm.fac[b][my_slot];  // [L0^-1'(i)][L1'(i+1)][L2'(i+2)]: row a = column a of L
+      VT w = yown;
       if (i + 1 < g.K) {
+        VT row[G2];
+        lds_run<VT, G2>(rec + BS + ac * G2, row);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= rec[BS + bb * G2 + ac] * xp1[bb];
+        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * xp1[bb];
       }
       if (i + 2 < g.K) {
+        VT row[G2];
+        lds_run<VT, G2>(rec + 2 * BS + ac * G2, row);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= rec[2 * BS + bb * G2 + ac] * xp2[bb];
+        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * xp2[bb];
       }
+      if (lane_ok) sm.xw[grp][al] = w;
+      __syncwarp(gmask);
+      VT wall[G2], row[G2];
+      lds_run<VT, G2>(&sm.xw[grp][0], wall);
+      lds_run<VT, G2>(rec + ac * G2, row);
       VT xv = VT(0);
 #pragma unroll
-      for (int bb = 0; bb < G2; ++bb) xv += rec[bb * G2 + ac] * __shfl_sync(gmask, w, bb, GS);
+      for (int bb = 0; bb < G2; ++bb) xv += row[bb] * wall[bb];
       if (node_ok) {
         a.theta_out[kP + off] = xv;
-        if (MU) acc0 += (double)xv * a.r[kP + off];
-        if (flex_dot) acc1 += (double)xv * a.y[kP + off];
+        if (MU) acc0 += (double)xv * r_own;
+        if (flex_dot) acc1 += (double)xv * y_own;
       }
+      if (lane_ok) sm.xy[grp][al] = xv;
+      __syncwarp(gmask);
 #pragma unroll
-      for (int bb = 0; bb < G2; ++bb) {
-        xp2[bb] = xp1[bb];
-        xp1[bb] = __shfl_sync(gmask, xv, bb, GS);
-      }
+      for (int bb = 0; bb < G2; ++bb) xp2[bb] = xp1[bb];
+      lds_run<VT, G2>(&sm.xy[grp][0], xp1);
     }
     __syncthreads();
   }
@@ -422,12 +467,12 @@ __global__ void __launch_bounds__(kSweepThreads) nbjm_sweep_kernel(Grid g, PrecD
   }
 }
 
-template <int NS, typename VT>
-constexpr size_t sweep_smem_bytes() { return sizeof(SweepSmem<NS, VT>); }
+template <int NS, typename VT, int THR>
+constexpr size_t sweep_smem_bytes() { return sizeof(SweepSmem<NS, VT, THR>); }
 
-template <int NS>
+template <int NS, int THR>
 inline unsigned sweep_blocks(const Grid& g) {
-  constexpr int TT = SweepGeom<NS>::TT;
+  constexpr int TT = SweepGeom<NS, THR>::TT;
   const int tiles = (g.T + 1 + TT - 1) / TT;
   return (unsigned)((long long)g.V * tiles);
 }

@@ -20,10 +20,13 @@ OK, EINVAL, ENOTPD, ENOCONV, EBREAKDOWN, ECUDA, ENOMEM, ETIMEOUT = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ECUDA",
                 6: "ENOMEM", 7: "ETIMEOUT"}
 OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS, OPT_PRECONDITIONER, OPT_KAPPA = 1, 2, 3, 4, 5, 6
+OPT_SWEEP_THREADS = 7
 
 EXPORTED = (
     "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
     "lq2d_solve_device", "lq2d_solve_nbjm_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_apply_delta_static",
+    "lq2d_autotune",
+    "lq2d_batch_create", "lq2d_batch_solve", "lq2d_batch_destroy", "lq2d_get_solution_device",
     "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
 )
@@ -80,7 +83,12 @@ def load() -> ctypes.CDLL:
         "lq2d_solve_nbjm_device": (i, [_vp, d, i, i, _vp, _vp, _vp, _ip, _dp, _vp]),
         "lq2d_apply_delta_device": (i, [_vp, _vp, _vp, _vp]),
         "lq2d_apply_precond_device": (i, [_vp, i, i, _vp, _vp, _vp]),
+        "lq2d_autotune": (i, [_vp, i, i, i, _ip, _dp, _vp]),
         "lq2d_apply_delta_static": (i, [i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lq2d_batch_create": (i, [pp, i, _vp]),
+        "lq2d_batch_solve": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp]),
+        "lq2d_batch_destroy": (None, [_vp]),
+        "lq2d_get_solution_device": (i, [_vp, _vp, _vp, _vp, _vp]),
         "lq2d_set_option": (i, [_vp, i, d]),
         "lq2d_get_stats": (i, [_vp, ctypes.POINTER(Stats)]),
         "lq2d_set_precision": (i, [_vp, i]),
@@ -226,6 +234,16 @@ class Problem:
     def apply_precond_device(self, S, L, d_r, d_q, stream=None):
         _check(load().lq2d_apply_precond_device(self._h, S, L, _addr(d_r), _addr(d_q), _stream(stream)))
 
+    def autotune(self, S=2, L=2, reps=5, stream=None):
+        """Times the sweep tile widths for this shape and precision mode and
+        keeps the faster; returns (threads, ms per preconditioner apply)."""
+        thr, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(load().lq2d_autotune(self._h, S, L, reps, ctypes.byref(thr), ctypes.byref(ms), _stream(stream)))
+        return thr.value, ms.value
+
+    def get_solution_device(self, x=None, u=None, costate=None, stream=None):
+        _check(load().lq2d_get_solution_device(self._h, _addr(x), _addr(u), _addr(costate), _stream(stream)))
+
     def set_option(self, option, value):
         _check(load().lq2d_set_option(self._h, option, float(value)))
 
@@ -253,3 +271,35 @@ class Problem:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Problems solved together by one graph launch (lq2d_batch_*)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (_vp * len(self.problems))(*[p._h.value for p in self.problems])
+        self._arr = arr
+        h = _vp()
+        _check(load().lq2d_batch_create(ctypes.byref(h), len(self.problems), arr))
+        self._h = h
+
+    def solve(self, tol=1e-8, S=2, L=2, max_iter=10000, stream=None, allow=(ENOCONV,)):
+        n = len(self.problems)
+        its = (ctypes.c_int * n)()
+        rel = (ctypes.c_double * n)()
+        sts = (ctypes.c_int * n)()
+        code = load().lq2d_batch_solve(self._h, tol, S, L, max_iter, its, rel, sts, _stream(stream))
+        _check(code, allow)
+        return dict(iterations=list(its), rel_kkt=list(rel), statuses=list(sts), status=code)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().lq2d_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

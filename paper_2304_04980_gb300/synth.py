@@ -72,9 +72,8 @@ def random_grid(K: int, N: int, T: int, n: int, m: int, seed: int, *,
     rng = np.random.default_rng(seed)
     nodes = K * N
     A_self = rng.standard_normal((nodes, n, n))
-    for p in range(nodes):
-        rad = np.max(np.abs(np.linalg.eigvals(A_self[p])))
-        A_self[p] *= rho / rad
+    rad = np.max(np.abs(np.linalg.eigvals(A_self)), axis=1)
+    A_self *= (rho / rad)[:, None, None]
     A_nbr = rng.standard_normal((nodes, 4, n, n)) * coupling
     B = rng.standard_normal((nodes, n, m))
     x0 = rng.standard_normal((nodes, n))
@@ -117,6 +116,8 @@ WORKLOADS = {
     "grid256_T200": dict(kind="random", K=256, N=256, T=200, n=4, m=2, seed=2, tol=1e-8),
     # profiling size: vectors of 52 MB, so one sweep's traffic exceeds the L2
     "grid128_T100": dict(kind="random", K=128, N=128, T=100, n=4, m=2, seed=3, tol=1e-8),
+    # profiling size with the K = N = 256 grid's parallelism, half its horizon
+    "grid256_T100": dict(kind="random", K=256, N=256, T=100, n=4, m=2, seed=2, tol=1e-8),
 }
 
 
@@ -125,6 +126,24 @@ def workload(name: str) -> GridLQ:
     if w["kind"] == "random":
         return random_grid(w["K"], w["N"], w["T"], w["n"], w["m"], w["seed"], name=name)
     return diffusion_grid(w["K"], w["N"], w["T"], w["n"], w["m"], w["seed"], name=name)
+
+
+def batch_grids(count: int = 512, seed: int = 3, n: int = 4, m: int = 2,
+                K_range=(8, 64), N_range=(8, 64), T_range=(50, 200),
+                coupling_range=(0.02, 0.2)) -> list:
+    """Uneven instances for the batched solve: K, N and T uniform integers in
+    their ranges and a coupling scale uniform in its range, drawn in that
+    order per instance from a master stream (PCG64, `seed`); instance idx
+    then uses the random_grid recipe with seed 10000 + idx."""
+    rng = np.random.default_rng(seed)
+    grids = []
+    for idx in range(count):
+        K = int(rng.integers(K_range[0], K_range[1] + 1))
+        N = int(rng.integers(N_range[0], N_range[1] + 1))
+        T = int(rng.integers(T_range[0], T_range[1] + 1))
+        c = float(rng.uniform(coupling_range[0], coupling_range[1]))
+        grids.append(random_grid(K, N, T, n, m, seed=10000 + idx, coupling=c, name="batch%d" % idx))
+    return grids
 
 
 def random_vector(shape, seed: int) -> np.ndarray:

@@ -1,0 +1,144 @@
+"""Batched solve (many uneven problems, one graph launch) through the C-ABI:
+each problem's result equals its own single solve bit for bit (same
+kernels, same order, deterministic reductions) and matches the oracle."""
+import numpy as np
+import pytest
+
+from oracle import lq2d_oracle as O
+from paper_2304_04980_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_04980_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def lq():
+    from paper_2304_04980_gb300 import lq2d
+    return lq2d
+
+
+def small_batch(count=10):
+    return synth.batch_grids(count, seed=17, K_range=(2, 9), N_range=(1, 9), T_range=(2, 14))
+
+
+def costate_of(prob, g, dev):
+    lam = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
+    prob.get_solution_device(costate=lam)
+    return lam.cpu().numpy()
+
+
+def test_batch_equals_single_solves_and_oracle(dev):
+    lq2d = lq()
+    grids = small_batch()
+    probs = [lq2d.Problem.from_grid(g) for g in grids]
+    batch = lq2d.Batch(probs)
+    out = batch.solve(1e-11, 2, 2, 5000)
+    assert out["status"] == 0 and all(s == 0 for s in out["statuses"])
+    batched = [costate_of(p, g, dev) for p, g in zip(probs, grids)]
+    for idx, (p, g) in enumerate(zip(probs, grids)):
+        single = p.solve(1e-11, 2, 2, 5000)
+        assert single["iterations"] == out["iterations"][idx]
+        assert np.array_equal(single["costate"], batched[idx])
+    for idx in (0, len(grids) - 1):
+        g = grids[idx]
+        ref = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())).solve(1e-12)
+        rel = np.linalg.norm(batched[idx] - ref.delta) / np.linalg.norm(ref.delta)
+        assert rel <= 1e-8
+    batch.close()
+
+
+def test_batch_rebuilds_and_sees_updated_data(dev):
+    lq2d = lq()
+    grids = small_batch(6)
+    probs = [lq2d.Problem.from_grid(g) for g in grids]
+    batch = lq2d.Batch(probs)
+    a = batch.solve(1e-10, 2, 2, 5000)
+    b = batch.solve(1e-6, 2, 2, 5000)          # new tolerance: graph rebuilt
+    assert all(x <= y for x, y in zip(b["iterations"], a["iterations"]))
+    probs[2].set_precision(1)                  # new mode for one problem: rebuilt
+    c = batch.solve(1e-10, 2, 2, 5000)
+    assert c["status"] == 0
+    # new initial state for one problem, same graph
+    g = grids[3]
+    x0 = synth.random_vector(g.x0.shape, seed=99)
+    g2 = g.with_x0(x0)
+    probs[3].update_device(*[torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in g2.arrays()])
+    d = batch.solve(1e-10, 2, 2, 5000)
+    assert d["status"] == 0
+    ref = O.Oracle(O.Problem.from_arrays(g2.K, g2.N, g2.T, g2.n, g2.m, *g2.arrays())).solve(1e-12)
+    lam = costate_of(probs[3], g2, dev)
+    assert np.linalg.norm(lam - ref.delta) <= 1e-7 * np.linalg.norm(ref.delta)
+    batch.close()
+
+
+def test_batch_reports_non_convergence_per_problem(dev):
+    lq2d = lq()
+    grids = small_batch(4)
+    probs = [lq2d.Problem.from_grid(g) for g in grids]
+    batch = lq2d.Batch(probs)
+    out = batch.solve(1e-12, 2, 2, 2)
+    assert out["status"] == lq2d.ENOCONV
+    assert all(s == lq2d.ENOCONV for s in out["statuses"])
+    assert all(it == 2 for it in out["iterations"])
+    batch.close()
+
+
+WIDTH_SHAPES = [(3, 5, 9, 1, 1), (4, 4, 20, 2, 1), (5, 6, 10, 3, 2), (9, 7, 33, 4, 2), (4, 5, 7, 5, 2),
+                (3, 4, 37, 6, 3), (4, 3, 6, 7, 2), (6, 3, 7, 8, 3)]
+
+
+@pytest.mark.parametrize("shape", WIDTH_SHAPES, ids=["K%dN%dT%dn%dm%d" % s for s in WIDTH_SHAPES])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sweep_width_256_matches_oracle(dev, shape, mode):
+    """The wider sweep tile (256 threads, twice the time steps per CTA) gives
+    the same preconditioner up to rounding and the same solution."""
+    lq2d = lq()
+    K, N, T, n, m = shape
+    g = synth.random_grid(K, N, T, n, m, seed=400 + 7 * K + 3 * N + T + n)
+    orc = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays()))
+    prob = lq2d.Problem.from_grid(g)
+    prob.set_precision(mode)
+    r = synth.random_vector((g.T + 1, g.nodes, g.n), seed=5)
+    rt = torch.from_numpy(r).to(dev)
+    q128 = torch.empty_like(rt)
+    prob.apply_precond_device(2, 2, rt, q128)
+    prob.set_option(lq2d.OPT_SWEEP_THREADS, 256)
+    q256 = torch.empty_like(rt)
+    prob.apply_precond_device(2, 2, rt, q256)
+    ref = orc.preconditioner(2, 2).apply(r.ravel())
+    bound = (1e-11 if mode == 0 else 1e-4) * np.abs(ref).max()
+    assert np.abs(q256.cpu().numpy().ravel() - ref).max() <= bound
+    assert np.abs(q128.cpu().numpy().ravel() - ref).max() <= bound
+    out = prob.solve(1e-10, 2, 2, 5000)
+    assert out["status"] == 0
+    lam = orc.solve(1e-12).delta
+    assert np.linalg.norm(out["costate"] - lam) <= 1e-7 * np.linalg.norm(lam)
+
+
+def test_autotune_picks_a_width_and_keeps_results(dev):
+    lq2d = lq()
+    g = synth.random_grid(16, 12, 40, 4, 2, seed=21)
+    prob = lq2d.Problem.from_grid(g)
+    base = prob.solve(1e-10, 2, 2, 5000)
+    thr, ms = prob.autotune(2, 2, 3)
+    assert thr in (128, 256) and ms > 0
+    out = prob.solve(1e-10, 2, 2, 5000)
+    assert out["status"] == 0
+    assert np.linalg.norm(out["costate"] - base["costate"]) <= 1e-8 * np.linalg.norm(base["costate"])
+    prob.set_precision(1)
+    thr32, _ = prob.autotune(2, 2, 3)
+    assert thr32 in (128, 256)
+    assert prob.solve(1e-10, 2, 2, 5000)["status"] == 0
+    with pytest.raises(lq2d.LQ2DError):
+        prob.set_option(lq2d.OPT_SWEEP_THREADS, 100)
+    with pytest.raises(lq2d.LQ2DError):
+        prob.autotune(2, 3, 1)

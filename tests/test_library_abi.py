@@ -76,3 +76,4 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lq2d_solve(None, 1e-8, 2, 2, 10, None, None, None, None, None, None) == lq2d.EINVAL
     assert lib.lq2d_set_option(None, 1, 0.0) == lq2d.EINVAL
     lib.lq2d_destroy(None)
+    assert lib.lq2d_autotune(None, 2, 2, 1, None, None, None) == lq2d.EINVAL
