@@ -154,6 +154,8 @@ int check_dims(int K, int N, int T, int n, int m) {
   const long long NN = (long long)K * N;
   if (NN * (T + 1) * (long long)n > (1LL << 40) || NN > (1LL << 30))
     return fail(LQ2D_EINVAL, "problem too large");
+  // the sweeps keep offsets within three grid rows of a plane in 32-bit ints
+  if (3LL * (N + 3) * (T + 1) > (1LL << 31) - 1) return fail(LQ2D_EINVAL, "grid rows too long (N * (T + 1))");
   return LQ2D_OK;
 }
 

@@ -131,11 +131,21 @@ struct SweepSmem {
   VT xw[Geo::TT][Geo::G2];            // per group: w of the current pair-row
   VT xy[Geo::TT][Geo::G2];            // per group: y or x of the current pair-row
   double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]
-  unsigned valid[NB];                 // [buffer] bit h: staged neighbour h inside the grid
 };
 
+// Register budget of the sweeps: one CTA per SM fewer than the shared-memory
+// footprint allows (233 KB per SM, 1 KB reserved per CTA), which leaves the
+// staging descriptors and the block rows in registers without spills.
+template <int NS, typename VT, int THR>
+constexpr int sweep_min_blocks() {
+  constexpr int by_smem = 232448 / ((int)sizeof(SweepSmem<NS, VT, THR>) + 1024) - 1;
+  constexpr int by_threads = 2048 / THR;
+  constexpr int b = by_smem < by_threads ? by_smem : by_threads;
+  return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
 template <int NS, int VAR, typename VT, int THR>
-__global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
+__global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
                                                          SolverState* st) {
   // VT = float is the mixed mode: FP32 factors, blocks and iterates, with
   // the flexible (Polak-Ribiere) ratio for the next direction
@@ -180,6 +190,87 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
   constexpr int CH = 16 / sizeof(VT);  // elements per 16-byte copy
   double acc0 = 0.0, acc1 = 0.0;
 
+  // ---- staging descriptors.  Element e of every staged array maps to a
+  // fixed shared-memory slot and to a global offset that advances by one
+  // grid row (N nodes) per pair-row, so each thread computes its share of
+  // the copies once: for halo elements an int offset within the plane (for
+  // pair-row 0, negative for the row above) and a packed word
+  //   bit 0 in range, bits 1-3 h, bits 4-5 di+1, bits 6-9 k, bits 10.. shared slot.
+  const unsigned long long packed = XI ? kXiPacked : kOmPacked;
+  constexpr int HALO_N = HALO ? Geo::NH * NS * HW : 0;
+  constexpr int HSL = (HALO_N + THR - 1) / THR > 0 ? (HALO_N + THR - 1) / THR : 1;
+  int h_off[HSL];
+  unsigned h_meta[HSL];
+#pragma unroll
+  for (int sl = 0; sl < HSL; ++sl) {
+    const int e = tid + sl * THR;
+    // component fastest, so that consecutive threads fill consecutive words
+    // of the [h][w][k] staging array (the shared slot is e itself)
+    const int h = e / (NS * HW), w = (e / NS) % HW, kk = e % NS;
+    const int tt = t0 - 1 + w;
+    const unsigned code = (unsigned)((packed >> (5 * (h & 7))) & 31ull);
+    const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
+    const bool ok = e < HALO_N && tt >= 0 && tt <= g.T && jn >= 0 && jn < g.N;
+    h_off[sl] = (di * g.N + jn) * Tp + tt;
+    h_meta[sl] = (ok ? 1u : 0u) | ((unsigned)(h & 7) << 1) | ((unsigned)(di + 1) << 4) | ((unsigned)kk << 6) |
+                 ((unsigned)(e < HALO_N ? e : 0) << 10);
+  }
+  // node blocks: runs of 5 n x n blocks per node (Omega~: Om of both nodes;
+  // Xi~: AQ and QAt of both nodes), 16-byte chunks where a run is a multiple
+  // of 16 bytes; word: bit 0 in range, bits 1-2 run, bits 3.. shared slot
+  constexpr int RUN = 5 * NS * NS;
+  constexpr int CB = (RUN * (int)sizeof(VT)) % 16 == 0 ? 16 / (int)sizeof(VT) : 1;
+  constexpr int NRUN = XI ? 4 : 2;
+  constexpr int BLK_N = HALO ? NRUN * (RUN / CB) : 0;
+  constexpr int BSL = (BLK_N + THR - 1) / THR > 0 ? (BLK_N + THR - 1) / THR : 1;
+  int b_off[BSL];
+  unsigned b_meta[BSL];
+#pragma unroll
+  for (int sl = 0; sl < BSL; ++sl) {
+    const int c = tid + sl * THR;
+    const int run = c / (RUN / CB), within = (c % (RUN / CB)) * CB;
+    const int cjj = run & 1;
+    const bool ok = c < BLK_N && (cjj == 0 || two_cols);
+    b_off[sl] = (j0 + cjj) * RUN + within;
+    b_meta[sl] = (ok ? 1u : 0u) | ((unsigned)(run & 3) << 1) |
+                 ((unsigned)((cjj * 10 + (run >= 2 ? 5 : 0)) * NS * NS + within) << 3);
+  }
+  // the pair-row's own entries for the tile (double): r, y, d, delta in the
+  // update sweep, else the source; word: bit 0 in range, bits 1-2 array,
+  // bits 3-6 k, bits 7.. shared slot
+  constexpr int NV = UPDATE ? 4 : 1;
+  constexpr int SRC_N = NV * 2 * NS * TT;
+  constexpr int SSL = (SRC_N + THR - 1) / THR;
+  int s_off[SSL];
+  unsigned s_meta[SSL];
+#pragma unroll
+  for (int sl = 0; sl < SSL; ++sl) {
+    const int e = tid + sl * THR;
+    const int vv = e / (2 * NS * TT), cjj = (e / (NS * TT)) % 2, kk = (e / TT) % NS, gg = e % TT;
+    const int tt = t0 + gg;
+    const bool ok = e < SRC_N && tt <= g.T && (cjj == 0 || two_cols);
+    s_off[sl] = (j0 + cjj) * Tp + tt;
+    s_meta[sl] = (ok ? 1u : 0u) | ((unsigned)(vv & 3) << 1) | ((unsigned)kk << 3) | ((unsigned)(e % (NV * 2 * NS * TT)) << 7);
+  }
+  // staged neighbours inside the grid, by pair-row: the column test is fixed
+  // for the CTA, the row test depends on whether the row above / below exists
+  unsigned col_ok = 0u, above = 0u, below = 0u;
+#pragma unroll
+  for (int h = 0; h < Geo::NH; ++h) {
+    const unsigned code = (unsigned)((packed >> (5 * h)) & 31ull);
+    const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
+    if (jn >= 0 && jn < g.N) col_ok |= 1u << h;
+    if (di < 0) above |= 1u << h;
+    if (di > 0) below |= 1u << h;
+  }
+  auto row_valid = [&](int i) -> unsigned {
+    unsigned m = col_ok;
+    if (i < 1) m &= ~above;
+    if (i + 1 >= g.K) m &= ~below;
+    return m;
+  };
+  const long long row_stride = (long long)g.N * Tp;
+
   // ---- staging of the forward step for pair-row i into buffer b
   auto stage_forward = [&](int i, int b) {
     // row-major L2, L1, L0^-1 (record blocks 3..5) of pair-row i, per class
@@ -187,41 +278,33 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
       const int c = e / (3 * BS), off = e % (3 * BS);
       cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + 3 * BS + off);
     }
-    {
-      // the pair-row's own entries: r, y, d, delta (update sweep) or src
-      constexpr int nv = UPDATE ? 4 : 1;
-      for (int e = tid; e < nv * 2 * NS * TT; e += THR) {
-        const int vv = e / (2 * NS * TT), cjj = (e / (NS * TT)) % 2, kk = (e / TT) % NS, gg = e % TT;
-        const int tt = t0 + gg;
-        if (tt > g.T || (cjj == 1 && !two_cols)) continue;
-        const double* base = UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src;
-        cp_async_8(&sm.src[b][vv][cjj][kk][gg], base + kk * g.Ps + (long long)(i * g.N + j0 + cjj) * Tp + tt);
-      }
+    const long long rb = (long long)i * row_stride;
+#pragma unroll
+    for (int sl = 0; sl < SSL; ++sl) {
+      const unsigned m = s_meta[sl];
+      if (!(m & 1u)) continue;
+      const int vv = (m >> 1) & 3;
+      const double* base = UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src;
+      cp_async_8(&sm.src[b][0][0][0][0] + (m >> 7), base + ((m >> 3) & 15) * g.Ps + rb + s_off[sl]);
     }
     if (HALO) {
-      const VT* vec = XI ? a.delta_s : a.theta_in;
-      for (int e = tid; e < Geo::NH * NS * HW; e += THR) {
-        const int h = e / (NS * HW), kk = (e / HW) % NS, w = e % HW;
-        const int tt = t0 - 1 + w;
-        if (tt < 0 || tt > g.T) continue;
-        const int q = staged_node(XI, h, i, j0, g.K, g.N);
-        if (q < 0) continue;
-        cp_async_elem(&sm.halo[b][h][w][kk], vec + kk * g.Ps + (long long)q * Tp + tt);
+      const VT* vec = (XI ? a.delta_s : a.theta_in) + rb;
+#pragma unroll
+      for (int sl = 0; sl < HSL; ++sl) {
+        const unsigned m = h_meta[sl];
+        const int ii = i + (int)((m >> 4) & 3u) - 1;
+        if (!(m & 1u) || ii < 0 || ii >= g.K) continue;
+        cp_async_elem(&sm.halo[b][0][0][0] + (m >> 10), vec + ((m >> 6) & 15) * g.Ps + h_off[sl]);
       }
-      constexpr int nb = XI ? 10 : 5;
-      for (int e = tid; e < 2 * nb * NS * NS; e += THR) {
-        const int cjj = e / (nb * NS * NS), bb = (e / (NS * NS)) % nb, rc = e % (NS * NS);
-        if (cjj == 1 && !two_cols) continue;
-        const int p = i * g.N + j0 + cjj;
-        const VT* srcb;
-        if (XI) srcb = (bb < 5 ? pd.AQ : pd.QAt) + ((size_t)p * 5 + (bb % 5)) * NS * NS + rc;
-        else srcb = pd.Om + ((size_t)p * 5 + bb) * NS * NS + rc;
-        cp_async_elem(&sm.blk[b][cjj][bb][rc], srcb);
-      }
-      if (tid == 0) {
-        unsigned m = 0;
-        for (int h = 0; h < Geo::NH; ++h) m |= (staged_node(XI, h, i, j0, g.K, g.N) >= 0 ? 1u : 0u) << h;
-        sm.valid[b] = m;
+      const long long bb = (long long)i * g.N * RUN;
+#pragma unroll
+      for (int sl = 0; sl < BSL; ++sl) {
+        const unsigned m = b_meta[sl];
+        if (!(m & 1u)) continue;
+        const int run = (m >> 1) & 3;
+        const VT* arr = XI ? (run >= 2 ? pd.QAt : pd.AQ) : pd.Om;
+        if constexpr (CB > 1) cp_async_16(&sm.blk[b][0][0][0] + (m >> 3), arr + bb + b_off[sl]);
+        else cp_async_elem(&sm.blk[b][0][0][0] + (m >> 3), arr + bb + b_off[sl]);
       }
     }
   };
@@ -250,13 +333,15 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
   cp_async_commit();
   for (int i = 0; i < g.K; ++i) {
     const int b = i % NB;
-    if (i + 2 < g.K) stage_forward(i + 2, (i + 2) % NB);
-    cp_async_commit();
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
-    cp_async_wait<2>();
+    // pair-row i has landed (only i+1 may be in flight); after the barrier
+    // every thread is done with step i-1, whose buffer takes pair-row i+2
+    cp_async_wait<1>();
     __syncthreads();
-    const unsigned valid = HALO ? sm.valid[b] : 0u;
+    if (i + 2 < g.K) stage_forward(i + 2, (i + 2) % NB);
+    cp_async_commit();
+    const unsigned valid = HALO ? row_valid(i) : 0u;
     VT tau = VT(0);
     if (node_ok) {
       if (UPDATE) {
@@ -363,7 +448,6 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
       for (int bb = 0; bb < G2; ++bb) ym2[bb] = ym1[bb];
       lds_run<VT, G2>(&sm.xy[grp][0], ym1);
     }
-    __syncthreads();  // buffer b is refilled NB - 2 steps later
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -379,8 +463,6 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
   for (int i = g.K - 1; i >= 0; --i) {
     const int step = g.K - 1 - i;
     const int b = step % NB;
-    if (i >= 2) stage_backward(i - 2, (step + 2) % NB);
-    cp_async_commit();
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
     VT yown = VT(0);
@@ -390,8 +472,10 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
       if (MU) r_own = a.r[kP + off];
       if (flex_dot) y_own = a.y[kP + off];
     }
-    cp_async_wait<2>();
+    cp_async_wait<1>();
     __syncthreads();
+    if (i >= 2) stage_backward(i - 2, (step + 2) % NB);
+    cp_async_commit();
     if (t >= 1) {
       const VT* rec = sm.fac[b][my_slot];  // [L0^-1'(i)][L1'(i+1)][L2'(i+2)]: row a = column a of L
       VT w = yown;
@@ -426,7 +510,6 @@ __global__ void __launch_bounds__(THR) nbjm_sweep_kernel(Grid g, PrecData<VT> pd
       for (int bb = 0; bb < G2; ++bb) xp2[bb] = xp1[bb];
       lds_run<VT, G2>(&sm.xy[grp][0], xp1);
     }
-    __syncthreads();
   }
   cp_async_wait<0>();
 

@@ -29,6 +29,9 @@ EXPORTED = (
     "lq2d_batch_create", "lq2d_batch_solve", "lq2d_batch_destroy", "lq2d_get_solution_device",
     "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
+    "lq2d_wsnet_create", "lq2d_wsnet_param_count", "lq2d_wsnet_set_params", "lq2d_wsnet_get_params",
+    "lq2d_wsnet_forward_device", "lq2d_wsnet_loss_grad_device", "lq2d_wsnet_train_step_device",
+    "lq2d_wsnet_destroy",
 )
 
 
@@ -94,6 +97,14 @@ def load() -> ctypes.CDLL:
         "lq2d_set_precision": (i, [_vp, i]),
         "lq2d_destroy": (None, [_vp]),
         "lq2d_last_error": (ctypes.c_char_p, []),
+        "lq2d_wsnet_create": (i, [pp, i, i, i, i, i, i, i, d]),
+        "lq2d_wsnet_param_count": (i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+        "lq2d_wsnet_set_params": (i, [_vp, _vp]),
+        "lq2d_wsnet_get_params": (i, [_vp, _vp]),
+        "lq2d_wsnet_forward_device": (i, [_vp, i, _vp, _vp, _vp, _vp]),
+        "lq2d_wsnet_loss_grad_device": (i, [_vp, i, _vp, _vp, _vp, _dp, _vp, _vp]),
+        "lq2d_wsnet_train_step_device": (i, [_vp, i, _vp, _vp, _vp, d, _dp, _vp]),
+        "lq2d_wsnet_destroy": (None, [_vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -296,6 +307,85 @@ class Batch:
     def close(self):
         if self._h is not None and self._h.value:
             load().lq2d_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WarmStartNet:
+    """The warm-start network of include/lq2d_warmstart.h: a stack of 3x3
+    convolutions over the grid mapping (x0, coupling scale) to delta^(0)."""
+
+    def __init__(self, K, N, T, n, channels=64, layers=6, max_batch=8, sigma=1.0):
+        self.K, self.N, self.T, self.n = K, N, T, n
+        self.channels, self.layers, self.max_batch, self.sigma = channels, layers, max_batch, sigma
+        h = _vp()
+        _check(load().lq2d_wsnet_create(ctypes.byref(h), K, N, T, n, channels, layers, max_batch, float(sigma)))
+        self._h = h
+        cnt = ctypes.c_longlong(0)
+        _check(load().lq2d_wsnet_param_count(self._h, ctypes.byref(cnt)))
+        self.param_count = cnt.value
+
+    def layer_sizes(self):
+        return [self.n + 1] + [self.channels] * (self.layers - 1) + [(self.T + 1) * self.n]
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if p.size != self.param_count:
+            raise ValueError("expected %d parameters, got %d" % (self.param_count, p.size))
+        _check(load().lq2d_wsnet_set_params(self._h, p.ctypes.data))
+
+    def get_params(self):
+        p = np.empty(self.param_count, dtype=np.float32)
+        _check(load().lq2d_wsnet_get_params(self._h, p.ctypes.data))
+        return p
+
+    def unflatten(self, flat):
+        """[(w [Cout][Cin][3][3], b [Cout]) per layer] from a parameter vector."""
+        sizes = self.layer_sizes()
+        out, off = [], 0
+        for l in range(self.layers):
+            ci, co = sizes[l], sizes[l + 1]
+            w = np.asarray(flat[off:off + co * ci * 9]).reshape(co, ci, 3, 3)
+            off += co * ci * 9
+            b = np.asarray(flat[off:off + co])
+            off += co
+            out.append((w, b))
+        return out
+
+    @staticmethod
+    def _coupling(c, batch):
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (batch,)))
+        return arr
+
+    def forward_device(self, batch, d_x0, coupling, d_delta0, stream=None):
+        c = self._coupling(coupling, batch)
+        _check(load().lq2d_wsnet_forward_device(self._h, batch, _addr(d_x0), c.ctypes.data, _addr(d_delta0),
+                                                _stream(stream)))
+
+    def loss_grad_device(self, batch, d_x0, coupling, d_target, want_grads=True, stream=None):
+        c = self._coupling(coupling, batch)
+        loss = ctypes.c_double(0.0)
+        g = np.empty(self.param_count, dtype=np.float32) if want_grads else None
+        _check(load().lq2d_wsnet_loss_grad_device(self._h, batch, _addr(d_x0), c.ctypes.data, _addr(d_target),
+                                                  ctypes.byref(loss), None if g is None else g.ctypes.data,
+                                                  _stream(stream)))
+        return loss.value, g
+
+    def train_step_device(self, batch, d_x0, coupling, d_target, lr, stream=None):
+        c = self._coupling(coupling, batch)
+        loss = ctypes.c_double(0.0)
+        _check(load().lq2d_wsnet_train_step_device(self._h, batch, _addr(d_x0), c.ctypes.data, _addr(d_target),
+                                                   float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().lq2d_wsnet_destroy(self._h)
         self._h = None
 
     def __del__(self):

@@ -149,3 +149,74 @@ def batch_grids(count: int = 512, seed: int = 3, n: int = 4, m: int = 2,
 def random_vector(shape, seed: int) -> np.ndarray:
     """A seeded standard-normal test vector (operator and preconditioner probes)."""
     return np.random.default_rng(seed).standard_normal(shape)
+
+
+@dataclasses.dataclass
+class WarmStartFamily:
+    """A spatially uniform grid family for the learned warm start: every node
+    shares one A_self, one neighbour block per direction and one B, drawn
+    once; an instance picks the coupling scale c that multiplies the
+    neighbour blocks and its own initial state x0."""
+    K: int
+    N: int
+    T: int
+    n: int
+    m: int
+    A_self: np.ndarray   # [n, n]
+    E_dir: np.ndarray    # [4, n, n] neighbour blocks before scaling (west, east, north, south)
+    B: np.ndarray        # [n, m]
+    r_weight: float
+    qT_weight: float
+    coupling_range: tuple
+
+    def instance_params(self, seed: int):
+        """(c, x0) of instance `seed`: c uniform in coupling_range, then x0
+        standard normal [K*N, n], from PCG64(seed)."""
+        rng = np.random.default_rng(seed)
+        c = float(rng.uniform(self.coupling_range[0], self.coupling_range[1]))
+        x0 = rng.standard_normal((self.K * self.N, self.n))
+        return c, x0
+
+    def grid(self, c: float, x0: np.ndarray) -> GridLQ:
+        nodes = self.K * self.N
+        A_nbr = np.broadcast_to(self.E_dir * c, (nodes, 4, self.n, self.n)).copy()
+        return GridLQ(self.K, self.N, self.T, self.n, self.m,
+                      np.broadcast_to(self.A_self, (nodes, self.n, self.n)).copy(), A_nbr,
+                      np.broadcast_to(self.B, (nodes, self.n, self.m)).copy(),
+                      _eye_blocks(nodes, self.n, 1.0), _eye_blocks(nodes, self.m, self.r_weight),
+                      _eye_blocks(nodes, self.n, self.qT_weight), np.ascontiguousarray(x0, dtype=np.float64),
+                      name="warm_c%.4f" % c)
+
+    def instance(self, seed: int) -> GridLQ:
+        return self.grid(*self.instance_params(seed))
+
+
+def warmstart_family(K: int = 128, N: int = 128, T: int = 100, n: int = 4, m: int = 2, seed: int = 5, *,
+                     rho: float = 0.95, r_weight: float = 0.1, qT_weight: float = 10.0,
+                     coupling_range=(0.02, 0.2)) -> WarmStartFamily:
+    """The learned-warm-start workload (K = N = 128, n = 4, m = 2, T = 100 by
+    default), with the random_grid recipe's distributions drawn once for the
+    whole grid: A_self standard normal scaled to spectral radius rho, the
+    four neighbour blocks standard normal, B standard normal (PCG64(seed), in
+    that order); Q = I, R = r_weight I, Q_T = qT_weight I."""
+    rng = np.random.default_rng(seed)
+    A_self = rng.standard_normal((n, n))
+    A_self *= rho / np.max(np.abs(np.linalg.eigvals(A_self)))
+    E_dir = rng.standard_normal((4, n, n))
+    B = rng.standard_normal((n, m))
+    return WarmStartFamily(K, N, T, n, m, A_self, E_dir, B, r_weight, qT_weight, tuple(coupling_range))
+
+
+def warmstart_init(layer_sizes, seed: int = 0, out_scale: float = 0.1) -> np.ndarray:
+    """Initial FP32 parameter vector of the warm-start network (layout of
+    include/lq2d_warmstart.h): He-normal weights, standard deviation
+    sqrt(2 / (9 C_in)), the last layer's times out_scale; zero biases.
+    Drawn layer by layer from PCG64(seed)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l in range(len(layer_sizes) - 1):
+        ci, co = layer_sizes[l], layer_sizes[l + 1]
+        std = np.sqrt(2.0 / (9.0 * ci)) * (out_scale if l + 2 == len(layer_sizes) else 1.0)
+        parts.append((rng.standard_normal(co * ci * 9) * std).astype(np.float32))
+        parts.append(np.zeros(co, dtype=np.float32))
+    return np.concatenate(parts)

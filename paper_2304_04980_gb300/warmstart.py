@@ -1,0 +1,130 @@
+"""Learned warm start of PCG: generate training pairs with the solver, train
+the network of include/lq2d_warmstart.h on the GPU, and solve from its
+guess.
+
+Algorithm 1 accepts any initial iterate delta^(0) (r^(0) = r_delta -
+Delta delta^(0)) and stops only on the tolerance, so the network can change
+how many iterations a solve takes but not what it converges to; a zero
+start remains the fallback.  Every arithmetic step (solver, network forward
+and backward passes, Adam) runs in the library's CUDA kernels; this module
+only moves buffers and loops.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import lq2d, synth
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class WarmStart:
+    """One network for one grid family (synth.WarmStartFamily)."""
+
+    def __init__(self, family: "synth.WarmStartFamily", channels: int = 64, layers: int = 6, batch: int = 8,
+                 sigma: float = 1.0, seed: int = 0, out_scale: float = 0.1, device: str = "cuda:0"):
+        torch = _torch()
+        self.family = family
+        self.batch = batch
+        self.dev = torch.device(device)
+        self.net = lq2d.WarmStartNet(family.K, family.N, family.T, family.n, channels, layers, batch, sigma)
+        self.net.set_params(synth.warmstart_init(self.net.layer_sizes(), seed, out_scale))
+        self.problem = None
+        self.x0 = None
+        self.targets = None
+        self.couplings = None
+        self.iterations = None
+
+    # -- data ----------------------------------------------------------
+    def _problem_for(self, g):
+        torch = _torch()
+        arrs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.dev) for a in g.arrays()]
+        if self.problem is None:
+            self.problem = lq2d.Problem.from_device(g.K, g.N, g.T, g.n, g.m, *arrs)
+        else:
+            self.problem.update_device(*arrs)
+        return self.problem
+
+    def generate(self, seeds, tol: float = 1e-6, precision: int = 1, S: int = 2, L: int = 2):
+        """Solves each instance (zero start) and keeps x0, c and the costates
+        on the device as training pairs.  Returns the wall time."""
+        torch = _torch()
+        f = self.family
+        count = len(seeds)
+        self.x0 = torch.empty((count, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.targets = torch.empty((count, f.T + 1, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.couplings = np.empty(count)
+        self.iterations = np.empty(count, dtype=np.int64)
+        t0 = time.perf_counter()
+        for idx, seed in enumerate(seeds):
+            c, x0 = f.instance_params(seed)
+            prob = self._problem_for(f.grid(c, x0))
+            prob.set_precision(precision)
+            out = prob.solve_device(tol, S, L, 100000, costate=self.targets[idx])
+            self.iterations[idx] = out["iterations"]
+            self.x0[idx].copy_(torch.from_numpy(x0))
+            self.couplings[idx] = c
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    # -- training --------------------------------------------------------
+    def fit(self, steps: int, lr: float = 1e-3, lr_final: float = 1e-4, seed: int = 0, log_every: int = 0):
+        """Adam steps on random minibatches of the generated pairs, with the
+        learning rate decayed geometrically from lr to lr_final.  Returns the
+        per-step losses."""
+        count = self.x0.shape[0]
+        rng = np.random.default_rng(seed)
+        losses = []
+        b = min(self.batch, count)
+        torch = _torch()
+        xb = torch.empty((b,) + tuple(self.x0.shape[1:]), dtype=torch.float64, device=self.dev)
+        tb = torch.empty((b,) + tuple(self.targets.shape[1:]), dtype=torch.float64, device=self.dev)
+        for s in range(steps):
+            idx = rng.choice(count, size=b, replace=False)
+            ii = torch.from_numpy(idx).to(self.dev)
+            torch.index_select(self.x0, 0, ii, out=xb)
+            torch.index_select(self.targets, 0, ii, out=tb)
+            rate = lr * (lr_final / lr) ** (s / max(1, steps - 1))
+            losses.append(self.net.train_step_device(b, xb, self.couplings[idx], tb, rate))
+            if log_every and (s % log_every == 0 or s + 1 == steps):
+                print("step %d loss %.4e lr %.2e" % (s, losses[-1], rate), flush=True)
+        return np.array(losses)
+
+    # -- use -------------------------------------------------------------
+    def guess(self, c: float, x0_dev, out=None):
+        """delta^(0) [T+1][K*N][n] of one instance (device tensor)."""
+        torch = _torch()
+        f = self.family
+        if out is None:
+            out = torch.empty((f.T + 1, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.net.forward_device(1, x0_dev, [c], out)
+        return out
+
+    def solve(self, seed: int, tol: float = 1e-8, warm: bool = True, precision: int = 0, S: int = 2, L: int = 2):
+        """Solves instance `seed` from the network's guess (warm) or from zero;
+        returns iterations, relative KKT residual, the costate and the time
+        of guess + solve (seconds, wall clock around synchronised calls)."""
+        torch = _torch()
+        f = self.family
+        c, x0 = f.instance_params(seed)
+        prob = self._problem_for(f.grid(c, x0))
+        prob.set_precision(precision)
+        lam = torch.empty((f.T + 1, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        x0d = torch.from_numpy(x0).to(self.dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d0 = self.guess(c, x0d) if warm else None
+        out = prob.solve_device(tol, S, L, 100000, delta0=d0, costate=lam)
+        torch.cuda.synchronize()
+        return dict(iterations=out["iterations"], rel_kkt=out["rel_kkt"], costate=lam,
+                    seconds=time.perf_counter() - t0, status=out["status"])
+
+    def close(self):
+        if self.problem is not None:
+            self.problem.close()
+        self.net.close()

@@ -1,5 +1,5 @@
 """CPU checks of the C-ABI library: it builds, loads without a GPU, exports
-every function declared in include/lq2d.h, and rejects bad arguments before
+every function declared in include/*.h, and rejects bad arguments before
 touching the device."""
 import ctypes
 import os
@@ -10,6 +10,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lq2d.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +22,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lq2d_[a-z_]+)\s*\(", text)))
 
@@ -77,3 +79,14 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lq2d_set_option(None, 1, 0.0) == lq2d.EINVAL
     lib.lq2d_destroy(None)
     assert lib.lq2d_autotune(None, 2, 2, 1, None, None, None) == lq2d.EINVAL
+
+
+def test_warmstart_net_rejects_bad_arguments_without_gpu(lib):
+    from paper_2304_04980_gb300 import lq2d
+    h = ctypes.c_void_p()
+    assert lib.lq2d_wsnet_create(ctypes.byref(h), 4, 4, 3, 9, 8, 2, 2, 1.0) == lq2d.EINVAL and not h.value
+    assert lib.lq2d_wsnet_create(ctypes.byref(h), 4, 4, 3, 2, 8, 2, 2, -1.0) == lq2d.EINVAL and not h.value
+    assert lib.lq2d_wsnet_create(ctypes.byref(h), 4, 4, 3, 2, 0, 2, 2, 1.0) == lq2d.EINVAL and not h.value
+    assert lib.lq2d_wsnet_forward_device(None, 1, None, None, None, None) == lq2d.EINVAL
+    assert lib.lq2d_wsnet_train_step_device(None, 1, None, None, None, 1e-3, None, None) == lq2d.EINVAL
+    lib.lq2d_wsnet_destroy(None)
