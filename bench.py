@@ -60,6 +60,11 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many uneven instances (K, N in 8..64, T in 50..200) "
                          "against solving them one after another")
+    ap.add_argument("--warmstart", type=int, default=0,
+                    help="learned warm start: train the network on this many solver-generated instances of the "
+                         "K = N = 128, T = 100 family, then time held-out solves from its guess and from zero")
+    ap.add_argument("--ws-steps", type=int, default=1500, help="training steps of the warm-start network")
+    ap.add_argument("--ws-eval", type=int, default=50, help="held-out instances (seeds 100000+) evaluated")
     return ap.parse_args()
 
 
@@ -575,8 +580,95 @@ def run_batch(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def conv_flops_per_sample(sizes, K, N):
+    """Multiply-adds x 2 of one forward pass of the 3x3 conv stack."""
+    return sum(2.0 * 9 * ci * co * K * N for ci, co in zip(sizes[:-1], sizes[1:]))
+
+
+def run_warmstart(args, dist):
+    """Learned warm start (K = N = 128, n = 4, m = 2, T = 100): training pairs
+    from the mixed-precision solver, Adam on the GPU, then held-out solves
+    to the tolerance from the network's guess and from zero (FP64 solver)."""
+    import torch
+
+    from paper_2304_04980_gb300 import lq2d, warmstart
+
+    lq2d.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    fam = synth.warmstart_family()
+    ws = warmstart.WarmStart(fam, channels=64, layers=6, batch=8, seed=0, device=str(dev))
+    gen_s = ws.generate(range(1000, 1000 + args.warmstart), tol=1e-6, precision=1)
+    sigma = float(ws.targets.std())
+    ws.net.close()
+    ws.net = lq2d.WarmStartNet(fam.K, fam.N, fam.T, fam.n, 64, 6, 8, sigma)
+    ws.net.set_params(synth.warmstart_init(ws.net.layer_sizes(), 0, 0.1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ws.fit(args.ws_steps, lr=1e-3, lr_final=5e-5)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    fl = conv_flops_per_sample(ws.net.layer_sizes(), fam.K, fam.N)
+    train_tflops = 3.0 * fl * 8 * args.ws_steps / train_s / 1e12
+    # warm-up of every path, then the held-out instances: zero and learned
+    # starts, each with the FP64 and the mixed-precision solver
+    combos = [("zero", False, 0), ("warm", True, 0), ("zero_mixed", False, 1), ("warm_mixed", True, 1)]
+    for _, warm, prec in combos:
+        ws.solve(99999, tol=args.tol, warm=warm, precision=prec)
+    its = {k: [] for k, _, _ in combos}
+    secs = {k: [] for k, _, _ in combos}
+    errs = []
+    for seed in range(100000, 100000 + args.ws_eval):
+        ref = None
+        for key, warm, prec in combos:
+            r = ws.solve(seed, tol=args.tol, warm=warm, precision=prec)
+            its[key].append(r["iterations"])
+            secs[key].append(r["seconds"])
+            if ref is None:
+                ref = r["costate"]
+            else:
+                errs.append(float(torch.linalg.norm(r["costate"] - ref) / torch.linalg.norm(ref)))
+    zero_it, warm_it, zero_s, warm_s = its["zero"], its["warm"], secs["zero"], secs["warm"]
+    x0 = torch.from_numpy(fam.instance_params(100000)[1]).to(dev)
+    ws.guess(0.1, x0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        ws.guess(0.1, x0)
+    e1.record()
+    torch.cuda.synchronize()
+    guess_ms = e0.elapsed_time(e1) / 10
+    zero_ms = 1e3 * float(np.mean(zero_s))
+    warm_ms = 1e3 * float(np.mean(warm_s))
+    line = {
+        "metric": "time-to-solve at 1e-8 rel KKT residual, learned warm start (ms)", "value": warm_ms, "unit": "ms",
+        "n_gpus": 1, "steps": args.ws_eval, "warmup": 2, "ms_per_step": warm_ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16 weights / f32 net", "data": "synthetic",
+        "config": {"workload": "warmstart K = N = 128, n = 4, m = 2, T = 100, coupling 0.02..0.2, x0 ~ N(0, 1)",
+                   "train_instances": args.warmstart, "train_steps": args.ws_steps, "batch": 8,
+                   "net": "6 x conv3x3, 64 channels, 404 outputs", "eval_instances": args.ws_eval, "tol": args.tol},
+        "zero_start_ms": zero_ms, "speedup_vs_zero_start": zero_ms / warm_ms,
+        "iterations_zero": float(np.mean(zero_it)), "iterations_warm": float(np.mean(warm_it)),
+        "max_rel_diff_vs_zero_fp64": max(errs), "guess_ms": guess_ms,
+        "mixed": {"zero_start_ms": 1e3 * float(np.mean(secs["zero_mixed"])),
+                  "warm_start_ms": 1e3 * float(np.mean(secs["warm_mixed"])),
+                  "iterations_zero": float(np.mean(its["zero_mixed"])),
+                  "iterations_warm": float(np.mean(its["warm_mixed"])),
+                  "speedup_warm_mixed_vs_zero_fp64": zero_ms / (1e3 * float(np.mean(secs["warm_mixed"])))},
+        "training": {"generate_s": gen_s, "train_s": train_s, "first_loss": float(np.mean(losses[:10])),
+                     "last_loss": float(np.mean(losses[-50:])), "conv_tflops_fp32": train_tflops,
+                     "solver_iterations_per_pair": float(np.mean(ws.iterations))},
+    }
+    ws.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.warmstart > 0:
+        run_warmstart(args, Dist())
+        return
     if args.batch > 0:
         run_batch(args, Dist())
         return

@@ -51,48 +51,21 @@ struct ConvArgs {
   int k_split;             // weight grad: pixels per split (multiple of BK)
 };
 
-// Element (k, n) of the B operand / (m, k) of the A operand, per mode.
-template <int MODE>
-__device__ __forceinline__ float load_a(const ConvArgs& a, int m, int k, int M, int K) {
-  if (m >= M || k >= K) return 0.f;
-  if (MODE == kFwd) return __bfloat162float(a.w[(size_t)m * K + k]);
-  if (MODE == kBwdData) {
-    const int o = k / 9, tap = k - 9 * o;
-    return __bfloat162float(a.w[((size_t)o * a.Cin + m) * 9 + tap]);
-  }
-  // weight grad: A = GY[o][q]
-  const int HW = a.H * a.W;
-  const int b = k / HW, pix = k - b * HW;
-  return a.gy[((size_t)b * a.Cout + m) * HW + pix];
-}
+// Operand gathering.  Element e = tid + 256 r (r = 0..3) of a 64 x 16 A
+// tile is (m = e / 16, k = e % 16) and of a 16 x 64 B tile is
+// (k = e / 64, n = e % 64), except the weight grad's B tile, which runs
+// along k: (k = e % 16, n = e / 16).  In every mode a thread's four
+// elements share one pixel (forward and input grad: its column n; weight
+// grad: its k), so the pixel is decoded once per K slice and the channel /
+// tap indices advance by 16 per slice without divisions.
 
-template <int MODE>
-__device__ __forceinline__ float load_b(const ConvArgs& a, int k, int n, int K, int N) {
-  if (k >= K || n >= N) return 0.f;
-  const int HW = a.H * a.W;
-  if (MODE == kFwd || MODE == kBwdData) {
-    const int c = k / 9, tap = k - 9 * c;
-    const int b = n / HW, pix = n - b * HW;
-    const int i = pix / a.W, j = pix - i * a.W;
-    const int di = tap / 3 - 1, dj = tap % 3 - 1;
-    if (MODE == kFwd) {
-      const int ii = i + di, jj = j + dj;
-      if (ii < 0 || ii >= a.H || jj < 0 || jj >= a.W) return 0.f;
-      return a.x[((size_t)b * a.Cin + c) * HW + ii * a.W + jj];
-    }
-    const int ii = i - di, jj = j - dj;
-    if (ii < 0 || ii >= a.H || jj < 0 || jj >= a.W) return 0.f;
-    return a.gy[((size_t)b * a.Cout + c) * HW + ii * a.W + jj];
-  }
-  // weight grad: B = X[c][q + tap], column Cin*9 is all ones (bias)
-  if (n == a.Cin * 9) return 1.f;
-  const int c = n / 9, tap = n - 9 * c;
-  const int b = k / HW, pix = k - b * HW;
-  const int i = pix / a.W, j = pix - i * a.W;
-  const int ii = i + tap / 3 - 1, jj = j + tap % 3 - 1;
-  if (ii < 0 || ii >= a.H || jj < 0 || jj >= a.W) return 0.f;
-  return a.x[((size_t)b * a.Cin + c) * HW + ii * a.W + jj];
+// (c, tap) of k + 16 from (c, tap) of k, tap in 0..8
+__device__ __forceinline__ void advance16(int& c, int& tap) {
+  tap += 7;
+  c += 1;
+  if (tap >= 9) { tap -= 9; c += 1; }
 }
+__device__ __forceinline__ int tap_row(int tap) { return (tap * 11) >> 5; }  // tap / 3 for 0 <= tap <= 8
 
 // C[M][N] = A[M][K] B[K][N] on a BM x BN tile per CTA, 4 x 4 outputs per
 // thread, the next K slice prefetched into registers while the current one
@@ -103,6 +76,7 @@ __global__ void __launch_bounds__(CT) conv_gemm_kernel(ConvArgs a, int M, int N,
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int HW = a.H * a.W;
   int k_begin = 0, k_end = K;
   if (MODE == kBwdWeight) {
     k_begin = blockIdx.z * a.k_split;
@@ -115,22 +89,116 @@ __global__ void __launch_bounds__(CT) conv_gemm_kernel(ConvArgs a, int M, int N,
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
 
-  // element e = tid + 256 r of a tile: A as (m = e / BK, k = e % BK); B as
-  // (k = e / BN, n = e % BN), except the weight grad, whose B runs along k
-  float ra[4], rb[4];
-  auto fetch = [&](int k0) {
+  // per-thread gather state
+  const int kl_a = tid % BK;              // k of the A elements (all modes)
+  const int ml_a = tid / BK;              // + 16 r: m of the A elements
+  int pb = 0, pi = 0, pj = 0;             // pixel (batch, row, column) of the thread's B column / k
+  bool pix_ok = false;
+  int cb[4], tb[4];                       // forward / input grad: (channel, tap) of the four B rows
+  int ca = 0, ta = 0;                     // input grad: (output channel, tap) of the A column
+  int wc[4], wt[4];                       // weight grad: (channel, tap) of the four B columns
+  if (MODE != kBwdWeight) {
+    const int n = n0 + tid % BN;
+    pix_ok = n < N;
+    pb = pix_ok ? n / HW : 0;
+    const int pix = pix_ok ? n - pb * HW : 0;
+    pi = pix / a.W;
+    pj = pix - pi * a.W;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int e = tid + CT * r;
-      const int k = k0 + e % BK;
-      ra[r] = load_a<MODE>(a, m0 + e / BK, k < k_end ? k : K, M, K);
-      if (MODE == kBwdWeight) {
-        const int kb = k0 + e % BK;
-        rb[r] = load_b<MODE>(a, kb < k_end ? kb : K, n0 + e / BK, K, N);
-      } else {
-        const int kb = k0 + e / BN;
-        rb[r] = load_b<MODE>(a, kb < k_end ? kb : K, n0 + e % BN, K, N);
+      const int k = k_begin + tid / BN + 4 * r;
+      cb[r] = k / 9;
+      tb[r] = k - 9 * cb[r];
+    }
+    if (MODE == kBwdData) {
+      const int k = k_begin + kl_a;
+      ca = k / 9;
+      ta = k - 9 * ca;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int n = n0 + tid / BK + 16 * r;
+      wc[r] = n / 9;
+      wt[r] = n - 9 * wc[r];
+    }
+  }
+
+  float ra[4], rb[4];
+  auto fetch = [&](int k0) {
+    if (MODE == kFwd) {
+      const int k = k0 + kl_a;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + ml_a + 16 * r;
+        ra[r] = (m < M && k < K) ? __bfloat162float(a.w[(size_t)m * K + k]) : 0.f;
       }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float v = 0.f;
+        const int k = k0 + tid / BN + 4 * r;
+        if (pix_ok && k < K) {
+          const int di = tap_row(tb[r]);
+          const int ii = pi + di - 1, jj = pj + tb[r] - 3 * di - 1;
+          if (ii >= 0 && ii < a.H && jj >= 0 && jj < a.W)
+            v = a.x[((size_t)pb * a.Cin + cb[r]) * HW + ii * a.W + jj];
+        }
+        rb[r] = v;
+      }
+    } else if (MODE == kBwdData) {
+      const int k = k0 + kl_a;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + ml_a + 16 * r;
+        ra[r] = (m < M && k < K) ? __bfloat162float(a.w[((size_t)ca * a.Cin + m) * 9 + ta]) : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float v = 0.f;
+        const int k = k0 + tid / BN + 4 * r;
+        if (pix_ok && k < K) {
+          const int di = tap_row(tb[r]);
+          const int ii = pi - di + 1, jj = pj - (tb[r] - 3 * di) + 1;
+          if (ii >= 0 && ii < a.H && jj >= 0 && jj < a.W)
+            v = a.gy[((size_t)pb * a.Cout + cb[r]) * HW + ii * a.W + jj];
+        }
+        rb[r] = v;
+      }
+    } else {
+      // weight grad: the thread's pixel is k = k0 + kl_a, for A and B alike
+      const int q = k0 + kl_a;
+      const bool ok = q < k_end;
+      const int b = ok ? q / HW : 0;
+      const int pix = ok ? q - b * HW : 0;
+      const int i = pix / a.W, j = pix - (pix / a.W) * a.W;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + ml_a + 16 * r;
+        ra[r] = (ok && m < M) ? a.gy[((size_t)b * a.Cout + m) * HW + pix] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int n = n0 + tid / BK + 16 * r;
+        float v = 0.f;
+        if (ok && n < N) {
+          if (n == a.Cin * 9) {
+            v = 1.f;
+          } else {
+            const int di = tap_row(wt[r]);
+            const int ii = i + di - 1, jj = j + wt[r] - 3 * di - 1;
+            if (ii >= 0 && ii < a.H && jj >= 0 && jj < a.W)
+              v = a.x[((size_t)b * a.Cin + wc[r]) * HW + ii * a.W + jj];
+          }
+        }
+        rb[r] = v;
+      }
+    }
+  };
+  auto advance = [&]() {
+    if (MODE != kBwdWeight) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) advance16(cb[r], tb[r]);
+      if (MODE == kBwdData) advance16(ca, ta);
     }
   };
   auto store = [&](int buf) {
@@ -145,11 +213,15 @@ __global__ void __launch_bounds__(CT) conv_gemm_kernel(ConvArgs a, int M, int N,
 
   int buf = 0;
   fetch(k_begin);
+  advance();
   store(0);
   __syncthreads();
   for (int k0 = k_begin; k0 < k_end; k0 += BK) {
     const bool more = k0 + BK < k_end;
-    if (more) fetch(k0 + BK);
+    if (more) {
+      fetch(k0 + BK);
+      advance();
+    }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       const float4 av = *reinterpret_cast<const float4*>(&As[buf][kk][tm]);
@@ -168,7 +240,6 @@ __global__ void __launch_bounds__(CT) conv_gemm_kernel(ConvArgs a, int M, int N,
     }
   }
 
-  const int HW = a.H * a.W;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int m = m0 + tm + r;
