@@ -241,7 +241,7 @@ def measured_hbm_gbs():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("kernels_hot.cuh", "common.cuh", "kernels.h"):
+    for name in ("sweep_tiled.cuh", "common.cuh", "kernels.h"):
         h.update(open(os.path.join(ROOT, "paper_2304_04980_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 

@@ -58,7 +58,7 @@ enum {
 /* Options for lq2d_set_option. */
 enum {
   LQ2D_OPT_STOP_MODE = 1,    /* 0: stop when ||r||_2 <= tol ||r_delta||_2 (default);
-                                1: stop when ||r||_inf < tol (Algorithm 1 line 11 as printed) */
+                                1: stop when ||r||_inf < tol (the stop test of Algorithm 1 as printed) */
   LQ2D_OPT_DRIVER = 2,       /* 0: the PCG loop runs on the device as a CUDA graph with a
                                    conditional while node (default);
                                 1: the host enqueues the steps, checking the stop flag every
@@ -166,7 +166,7 @@ int lq2d_solve_device(lq2d_problem *h, double tol, int outer_S, int inner_L, int
 /* Algorithm 2 run as a solver: the "standard nested block Jacobi method" the
  * paper compares PCGM against (Section V).  Each outer step runs inner_L
  * sweeps (L = 2 in the paper) and stops when
- * ||delta^(s+1) - delta^(s)||_inf < eps (the exit line of Algorithm 2).
+ * ||delta^(s+1) - delta^(s)||_inf < eps (the exit test of Algorithm 2).
  * Each inner iteration starts from the current outer iterate, theta^(0) =
  * delta^(s): with a zero inner start at every outer step, as printed, the
  * fixed point would be (Upsilon_L^-1 - Xi~)^-1 r_delta instead of the
@@ -178,7 +178,7 @@ int lq2d_solve_nbjm_device(lq2d_problem *h, double eps, int inner_L, int max_out
                            void *d_x, void *d_u, void *d_costate,
                            int *outer_iterations, double *rel_kkt_residual, void *stream);
 
-/* y = Delta d (Section II-B, the product of Algorithm 1 line 7), device
+/* y = Delta d (Section II-B, the operator product of Algorithm 1), device
  * buffers [T+1][K*N][n].  Returns after the work on `stream` is complete. */
 int lq2d_apply_delta_device(lq2d_problem *h, const void *d_in, void *d_out, void *stream);
 

@@ -386,7 +386,7 @@ def nbjm_solve(Sp: Splitting, r_delta: np.ndarray, L: int, eps: float, max_outer
                phi: Optional["PhiSolver"] = None, inner_start: str = "outer") -> NBJMResult:
     """Algorithm 2 as a solver (the paper's "standard nested block Jacobi",
     Section V): outer iterations with L inner sweeps each, until
-    ||delta^(s+1) - delta^(s)||_inf < eps (its exit line; reading A8 keeps
+    ||delta^(s+1) - delta^(s)||_inf < eps (its exit test; reading A8 keeps
     this exit out of the preconditioner).
 
     inner_start="outer" (reading A22) starts every inner iteration from the
@@ -458,30 +458,30 @@ def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray
     it = 0
     restarts = 0
     while True:
-        r = r_delta - Delta @ delta                       # line 2
+        r = r_delta - Delta @ delta                       # initial residual
         hist.append(np.linalg.norm(r))
         if passed(r):                                     # reading A10
             return PCGResult(delta, it, True, hist, restarts, alphas, betas)
         if it >= max_iter:
             return PCGResult(delta, it, False, hist, restarts, alphas, betas)
-        d = precond(r)                                    # line 3
-        mu = d @ r                                        # line 4
+        d = precond(r)                                    # first direction
+        mu = d @ r
         converged = False
-        while it < max_iter:                              # line 6
-            y = Delta @ d                                 # line 7
-            theta = mu / (y @ d)                          # line 8
+        while it < max_iter:
+            y = Delta @ d                                 # operator product
+            theta = mu / (y @ d)                          # step length
             alphas.append(theta)
-            delta = delta + theta * d                     # line 9
-            r = r - theta * y                             # line 10
+            delta = delta + theta * d                     # iterate
+            r = r - theta * y                             # residual
             it += 1
             hist.append(np.linalg.norm(r))
-            if passed(r):                                 # line 11
+            if passed(r):                                 # stop test
                 converged = True
                 break
-            q = precond(r)                                # line 12
-            mu_new = q @ r                                # line 13
+            q = precond(r)                                # preconditioner
+            mu_new = q @ r
             betas.append(mu_new / mu)
-            d = q + (mu_new / mu) * d                     # line 14
+            d = q + (mu_new / mu) * d                     # next direction
             mu = mu_new
         if not converged:
             return PCGResult(delta, it, False, hist, restarts, alphas, betas)

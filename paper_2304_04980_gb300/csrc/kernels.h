@@ -81,7 +81,7 @@ struct KernelTable {
   void (*delta_z_f32op)(const Grid& g, const OpData<float>& op, const float* q, const float* dold32, float* z,
                         const SolverState* st, int use_beta, cudaStream_t s);
   // y = A~ z + B~ R~^-1 B~' dn; in loop mode also writes dn into dout, reduces
-  // y' dn and sets vartheta = mu / (y' dn) (Algorithm 1 lines 7-8)
+  // y' dn and sets vartheta = mu / (y' dn) (Algorithm 1: operator product and step length)
   void (*delta_y)(const Grid& g, const OpData<double>& op, const double* z, const double* q, const double* dold,
                   double* dout, double* y, double* partials, SolverState* st, int loop_mode, cudaStream_t s);
   void (*delta_y_f32)(const Grid& g, const OpData<double>& op, const double* z, const float* q, const double* dold,
@@ -113,7 +113,7 @@ const KernelTable* kernel_table(int n);
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
                        int keep_iter, double* hist, int hist_cap, double phase_rho2, cudaStream_t s);
 // identity preconditioner (plain CG): q = r, mu = r'r; with update, the PCG
-// update of Algorithm 1 lines 9-11 first
+// update and stop test of Algorithm 1 first
 void launch_ident(const Grid& g, bool update, double* r, double* delta, const double* y, const double* d,
                   double* q, double* partials, SolverState* st, cudaStream_t s);
 // standalone NBJM exit test: max |a - b| (b = NULL: max |a|) < eps, counts the outer step

@@ -28,8 +28,9 @@ __device__ __forceinline__ auto ahat_col(const D& nd, int r, int dir) {
 // Delta apply, part 1: z = Q~^-1 A~' dn, one thread per (node, t).
 //   (A~' dn)_t = -dn_t + A_hat' dn_{t+1}   (t < T),   (A~' dn)_T = -dn_T
 //   z_t = Q_t^-1 (A~' dn)_t                 (Q_T at t = T)
-// dn = q + beta d_old is formed on the fly (Algorithm 1 line 14 fused into
-// line 7); beta comes from the device state.
+// dn = q + beta d_old is formed on the fly (the direction update of
+// Algorithm 1 fused into its operator product); beta comes from the device
+// state.
 // ---------------------------------------------------------------------------
 template <int NS, typename QT, typename CT, typename DT>
 __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> nd, const QT* __restrict__ q,
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
 // ---------------------------------------------------------------------------
 // Delta apply, part 2: y = A~ z + B~ R~^-1 B~' dn, one thread per (node, t).
 //   y_0 = -z_0,   y_t = A_hat z_{t-1} - z_t + S dn_t   (t >= 1, S = B R^-1 B')
-// Loop mode (Algorithm 1 lines 7-8, 14): dn = q + beta d_old is written back
+// Loop mode (Algorithm 1: operator product, step length, direction update): dn = q + beta d_old is written back
 // to d (each thread owns its entry), y' dn is reduced and vartheta set.
 // ---------------------------------------------------------------------------
 template <int NS, bool LOOP, typename QT, typename CT>

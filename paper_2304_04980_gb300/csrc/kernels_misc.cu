@@ -53,7 +53,7 @@ __global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int
 }
 
 // Identity preconditioner (plain CG, used to estimate kappa(Delta)): q = r
-// and mu = r'r.  With UPDATE, Algorithm 1 lines 9-11 come first (delta +=
+// and mu = r'r.  With UPDATE, the update and stop test of Algorithm 1 come first (delta +=
 // vartheta d, r -= vartheta y, stop test), and mu is the new ||r||^2.
 template <bool UPDATE>
 __global__ void ident_kernel(Grid g, double* __restrict__ r, double* __restrict__ delta,
@@ -102,7 +102,7 @@ __global__ void ident_kernel(Grid g, double* __restrict__ r, double* __restrict_
   }
 }
 
-// Exit test of the standalone NBJM solver (Algorithm 2's last line):
+// Exit test of the standalone NBJM solver (Algorithm 2's exit test):
 // ||a - b||_inf < eps, b = NULL meaning zero; counts the outer step.
 template <typename VT>
 __global__ void nbjm_diff_kernel(Grid g, const VT* __restrict__ a, const VT* __restrict__ b, double* partials,
@@ -127,7 +127,7 @@ __global__ void nbjm_diff_kernel(Grid g, const VT* __restrict__ a, const VT* __r
   }
 }
 
-// r^(0) = r_delta - Delta delta^(0) (Algorithm 1 line 2) with y = Delta delta^(0)
+// r^(0) = r_delta - Delta delta^(0) (Algorithm 1, initial residual) with y = Delta delta^(0)
 // given (or zero), delta = delta^(0); then the initial stop test (reading:
 // no iterations when r^(0) already passes).
 __global__ void init_residual_kernel(Grid g, const double* __restrict__ rhs, const double* __restrict__ y,

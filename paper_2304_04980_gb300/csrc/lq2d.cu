@@ -322,8 +322,8 @@ int create_common(lq2d_problem** out, int K, int N, int T, int n, int m, const d
 }
 
 // One preconditioner application q = D_S r_in (Algorithm 2, S x L sweeps
-// from zero starts).  fuse_update: the first sweep also performs Algorithm 1
-// lines 9-11; mu: the last sweep reduces mu = q' r.  Returns the buffer
+// from zero starts).  fuse_update: the first sweep also performs the update
+// and stop test of Algorithm 1; mu: the last sweep reduces mu = q' r.  Returns the buffer
 // holding q (thB, since S*L is even); its elements are double in FP64 mode
 // and float in the mixed mode.
 template <typename VT>
@@ -424,7 +424,7 @@ void enqueue_delta(lq2d_problem* h, const void* q, const double* dold, double* d
   if (timing) cudaEventRecord(e1, s);
 }
 
-// One PCG step (Algorithm 1 lines 7-14): y = Delta d with d = q + beta d
+// One PCG step (Algorithm 1, operator product to next direction): y = Delta d with d = q + beta d
 // fused in, then the preconditioner with the update fused into its first
 // sweep and mu into its last.
 void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
@@ -872,7 +872,7 @@ int solve_nbjm_impl(lq2d_problem* h, double eps, int L, int max_outer, double* d
 }
 
 // The part of a solve before the device loop: state, r^(0) = r_delta,
-// q = P^-1 r^(0) with mu, d = 0 (Algorithm 1 lines 1-5).
+// q = P^-1 r^(0) with mu, d = 0 (the start of Algorithm 1).
 void enqueue_solve_init(lq2d_problem* h, double tol, int S, int L, int max_iter, cudaStream_t s) {
   const Grid& g = h->g;
   const double phase_rho2 = h->precision == 2 ? kPhaseRho * kPhaseRho : 0.0;

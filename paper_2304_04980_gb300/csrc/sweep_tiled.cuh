@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   if (UPDATE) {
     double tot0, tot1;
     if (grid_reduce2<true>(acc0, acc1, a.partials, &st->counters[kCntNorm], &tot0, &tot1)) {
-      // Algorithm 1 line 11, with the stop rule selected by stop_mode
+      // the stop test of Algorithm 1, with the rule selected by stop_mode
       st->rnorm2 = tot0;
       st->rnorm_inf = tot1;
       const int it = st->iter + 1;
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   if (MU) {
     double tot0, tot1;
     if (grid_reduce2<false>(acc0, acc1, a.partials, &st->counters[kCntMu], &tot0, &tot1)) {
-      // Algorithm 1 lines 13-14: mu^(i+1) and the ratio used for d^(i+1);
+      // Algorithm 1: mu^(i+1) and the ratio used for d^(i+1);
       // the mixed mode takes q^(i+1)'(r^(i+1) - r^(i)) / mu^(i), which equals
       // mu^(i+1) / mu^(i) for an exactly symmetric preconditioner
       if (!(tot0 > 0.0) || !isfinite(tot0) || !isfinite(tot1)) {
