@@ -73,12 +73,12 @@ enum {
                                   extreme eigenvalues of the preconditioned operator (Lanczos
                                   matrix of CG; Section V reports kappa before and after
                                   preconditioning); read them with lq2d_get_stats */
-  LQ2D_OPT_SWEEP_THREADS = 7  /* 128 (default) or 256: threads per CTA of the NBJM sweeps, i.e.
-                                  a tile of 128/g or 256/g time steps per CTA (g = 2n rounded
-                                  up to a power of two); sets the FP64 and FP32 sweeps alike.
-                                  lq2d_autotune picks it by timing. Results may differ in
-                                  the last bits between widths (partial sums are grouped per
-                                  CTA) */
+  LQ2D_OPT_SWEEP_THREADS = 7  /* 32, 64, 128 or 256: threads per CTA of the NBJM sweeps, i.e. a
+                                  tile of threads/g time steps per CTA (g = 2n rounded up to a
+                                  power of two); sets the FP64 and FP32 sweeps alike.
+                                  Default 64; lq2d_autotune picks it by timing.  Results may
+                                  differ in the last bits between widths (partial sums are
+                                  grouped per CTA) */
 };
 
 /* Statistics of the last solve on a handle. */
@@ -190,7 +190,7 @@ int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const v
 /* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS) for this problem's shape
  * and the handle's current precision mode by timing: runs D_S (S outer x L
  * inner sweeps, Algorithm 2) once as warm-up and then `reps` times with each
- * candidate width (128, 256), with CUDA events on `stream`, and keeps the
+ * candidate width (32, 64, 128, 256), with CUDA events on `stream`, and keeps the
  * faster for later solves of this precision mode (FP64 and FP32 sweeps keep
  * separate choices).  The problem's right-hand side is the input; the
  * handle's solution buffers are not touched.

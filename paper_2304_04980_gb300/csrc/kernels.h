@@ -8,7 +8,12 @@
 namespace lq2d {
 
 constexpr int kOpThreads = 256;     // threads per block of the node-time kernels
-constexpr int kSweepThreads = 128;  // default threads per block of the sweep kernels (128 or 256)
+// Default threads per block of the sweep kernels (32, 64, 128 or 256 are
+// compiled).  Two warps per CTA spread the (column pair, time step) block
+// solves over the SMs in fine units, each staging a factor row once for
+// 64/g time steps (g = 2n rounded up to a power of two); this width timed
+// fastest on the 64 x 64 x 100 and 256 x 256 x 200 grids in both precisions.
+constexpr int kSweepThreads = 64;
 
 // Operands of the Delta product in its compute precision CT (double, or
 // float in precision mode 2): the grid blocks and the per-node Q^-1, Q_T^-1,
@@ -91,8 +96,8 @@ struct KernelTable {
                         double* dout, float* dout32, double* y, double* partials, SolverState* st, int loop_mode,
                         cudaStream_t s);
   // FP64 sweep (Algorithm 2 step); the OmegaMu variant sets beta = mu_new / mu_old
-  // threads: CTA width of the sweep, 128 or 256 (a tile of threads / 2n time
-  // steps, 2n rounded up to a power of two)
+  // threads: CTA width of the sweep, 32, 64, 128 or 256 (a tile of threads / 2n
+  // time steps, 2n rounded up to a power of two)
   void (*sweep)(int variant, int threads, const Grid& g, const PrecData<double>& pd, const SweepArgsT<double>& a,
                 SolverState* st, cudaStream_t s);
   // FP32 sweep of the mixed mode; the OmegaMu variant sets the flexible

@@ -301,13 +301,17 @@ void launch_sweep_t(int variant, const Grid& g, const PrecData<VT>& pd, const Sw
   }
 }
 
-// Sweep launch with the CTA width (threads) chosen for the problem: 128 or
-// 256 threads, i.e. a tile of 128/GS or 256/GS time steps per CTA.
+// Sweep launch with the CTA width (threads) chosen for the problem: 32, 64,
+// 128 or 256 threads, i.e. a tile of threads/GS time steps per CTA.
 template <int NS, typename VT>
 void launch_sweep(int variant, int threads, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a,
                   SolverState* st, cudaStream_t s) {
-  if (threads == 256) launch_sweep_t<NS, VT, 256>(variant, g, pd, a, st, s);
-  else launch_sweep_t<NS, VT, 128>(variant, g, pd, a, st, s);
+  switch (threads) {
+    case 32: launch_sweep_t<NS, VT, 32>(variant, g, pd, a, st, s); break;
+    case 64: launch_sweep_t<NS, VT, 64>(variant, g, pd, a, st, s); break;
+    case 256: launch_sweep_t<NS, VT, 256>(variant, g, pd, a, st, s); break;
+    default: launch_sweep_t<NS, VT, 128>(variant, g, pd, a, st, s); break;
+  }
 }
 
 // Allows every sweep instantiation its shared-memory footprint (above the
@@ -331,7 +335,9 @@ cudaError_t prepare_sweeps_t() {
 
 template <int NS>
 cudaError_t prepare_sweeps() {
-  cudaError_t e[4] = {prepare_sweeps_t<NS, double, 128>(), prepare_sweeps_t<NS, float, 128>(),
+  cudaError_t e[8] = {prepare_sweeps_t<NS, double, 32>(),  prepare_sweeps_t<NS, float, 32>(),
+                      prepare_sweeps_t<NS, double, 64>(),  prepare_sweeps_t<NS, float, 64>(),
+                      prepare_sweeps_t<NS, double, 128>(), prepare_sweeps_t<NS, float, 128>(),
                       prepare_sweeps_t<NS, double, 256>(), prepare_sweeps_t<NS, float, 256>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;

@@ -259,9 +259,17 @@ __global__ void setup_omega_kernel(SetupBuffers sb, int K, int N, int n) {
 //   L0_i L0_i' = A_{i,i} - L1_i L1_i' - L2_i L2_i'
 // The diagonal factors are stored inverted.  A missing second column (odd N)
 // is carried as a decoupled identity block, whose solution is zero.
-// Record of pair-row i (G2 = 2n, blocks G2 x G2 row-major):
-//   [L2'][L1'][L0^-1'] (read by the forward substitution)
-//   [L2 ][L1 ][L0^-1 ] (read by the backward substitution)
+// The substitutions are stored pre-multiplied by the inverted pivots, so
+// that each step of a sweep is one product with the known right-hand side
+// plus products with the two previous results:
+//   forward  (L y = tau):   y_i = L0_i^-1 tau_i - M1_i y_{i-1} - M2_i y_{i-2},
+//                           M1_i = L0_i^-1 L1_i,  M2_i = L0_i^-1 L2_i
+//   backward (L' x = y):    x_i = L0_i^-T y_i - N1_i x_{i+1} - N2_i x_{i+2},
+//                           N1_i = L0_i^-T L1_{i+1}',  N2_i = L0_i^-T L2_{i+2}'
+// (N1, N2 are zero past the last pair-row).  Record of pair-row i (G2 = 2n,
+// blocks G2 x G2 row-major, so a lane's row is contiguous):
+//   [N2_i][N1_i][L0_i^-T]   (backward step i)
+//   [M2_i][M1_i][L0_i^-1]   (forward step i)
 __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V, long long fac_rec,
                                     long long fac_vc, int* status) {
   extern __shared__ double smem[];
@@ -362,6 +370,28 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       }
       __syncwarp();
     }
+    // --- backward blocks of the two previous records, now that L1_i and
+    //     L2_i exist: N1_{i-1} = L0_{i-1}^-T L1_i', N2_{i-2} = L0_{i-2}^-T L2_i'
+    double* rec_base = sb.fac + (size_t)vc * fac_vc;
+    if (i >= 1) {
+      double* rp = rec_base + (size_t)(i - 1) * fac_rec;
+      for (int e = lane; e < BS; e += 32) {
+        const int a = e / G2, b = e % G2;
+        double s = 0.0;
+        for (int c = 0; c < G2; ++c) s += L0m1[c * G2 + a] * L1[b * G2 + c];
+        rp[1 * BS + e] = s;
+      }
+    }
+    if (i >= 2) {
+      double* rp = rec_base + (size_t)(i - 2) * fac_rec;
+      for (int e = lane; e < BS; e += 32) {
+        const int a = e / G2, b = e % G2;
+        double s = 0.0;
+        for (int c = 0; c < G2; ++c) s += L0m2[c * G2 + a] * L2[b * G2 + c];
+        rp[0 * BS + e] = s;
+      }
+    }
+    __syncwarp();
     // --- L0^-1 into the slot of pair-row i-2 (no longer needed); lane c
     //     solves column c of L0 X = I by forward substitution
     double* L0i = prevL0 + (cur ^ 1) * BS;
@@ -375,16 +405,21 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       }
     }
     __syncwarp();
-    // --- store the record
-    double* rec = sb.fac + (size_t)vc * fac_vc + (size_t)i * fac_rec;
+    // --- record of pair-row i: the backward blocks N2_i, N1_i start at
+    //     zero and are filled by the next two pair-rows
+    double* rec = rec_base + (size_t)i * fac_rec;
     for (int e = lane; e < BS; e += 32) {
       const int a = e / G2, b = e % G2;
-      const int et = b * G2 + a;  // transposed position
-      rec[0 * BS + et] = L2[e];
-      rec[1 * BS + et] = L1[e];
-      rec[2 * BS + et] = L0i[e];
-      rec[3 * BS + e] = L2[e];
-      rec[4 * BS + e] = L1[e];
+      double m1 = 0.0, m2 = 0.0;
+      for (int c = 0; c <= a; ++c) {
+        m1 += L0i[a * G2 + c] * L1[c * G2 + b];
+        m2 += L0i[a * G2 + c] * L2[c * G2 + b];
+      }
+      rec[0 * BS + e] = 0.0;
+      rec[1 * BS + e] = 0.0;
+      rec[2 * BS + e] = L0i[b * G2 + a];
+      rec[3 * BS + e] = m2;
+      rec[4 * BS + e] = m1;
       rec[5 * BS + e] = L0i[e];
       prevL1[e] = L1[e];
     }

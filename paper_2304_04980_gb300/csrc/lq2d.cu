@@ -91,7 +91,7 @@ struct lq2d_problem {
   float* f32_buf = nullptr;  // FP32 copies of the factors and node blocks (mode 1, allocated on first use)
   float* d32 = nullptr;      // FP32 copy of the direction d (mode 2)
   int precond_kind = 0;      // 0: NBJM (Algorithm 2), 1: none (plain CG)
-  int sweep_threads[2] = {kSweepThreads, kSweepThreads};  // CTA width of the FP64 / FP32 sweeps (128 or 256)
+  int sweep_threads[2] = {kSweepThreads, kSweepThreads};  // CTA width of the FP64 / FP32 sweeps (32..256)
   int kappa = 0;             // record the PCG coefficients and estimate the condition number
   double* hist = nullptr;    // device: vartheta_j, beta_j pairs
   std::vector<double> h_hist;
@@ -1132,11 +1132,11 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
     cudaEventDestroy(e0);
     return fail(LQ2D_ECUDA, "cudaEventCreate failed");
   }
-  const int cand[2] = {128, 256};
+  const int cand[4] = {32, 64, 128, 256};
   double best_ms = 0.0;
   int best = saved;
   cudaError_t err = cudaSuccess;
-  for (int c = 0; c < 2 && err == cudaSuccess; ++c) {
+  for (int c = 0; c < 4 && err == cudaSuccess; ++c) {
     h->sweep_threads[slot] = cand[c];
     enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);  // warm-up
     cudaEventRecord(e0, s);
@@ -1296,7 +1296,8 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
       h->max_restarts = v;
       return LQ2D_OK;
     case LQ2D_OPT_SWEEP_THREADS:
-      if (v != 128 && v != 256) return fail(LQ2D_EINVAL, "sweep threads must be 128 or 256");
+      if (v != 32 && v != 64 && v != 128 && v != 256)
+        return fail(LQ2D_EINVAL, "sweep threads must be 32, 64, 128 or 256");
       h->sweep_threads[0] = h->sweep_threads[1] = v;
       return LQ2D_OK;
     default:

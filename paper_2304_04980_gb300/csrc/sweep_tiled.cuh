@@ -16,15 +16,18 @@
 //     delta^(s) (Xi~ term, t-1 and t+1) for the TT steps: contiguous runs
 //     in the component-plane layout;
 //   * the Omega~ / Xi~ node blocks of the pair-row's two nodes.
-// Per pair-row i:
-//   forward:  y_i = L0_i^-1 (tau_i - L1_i y_{i-1} - L2_i y_{i-2})
-//   backward: x_i = L0_i^-T (y_i - L1_{i+1}' x_{i+1} - L2_{i+2}' x_{i+2})
-// Each lane computes one row of every block product; the forward pass reads
-// the row-major blocks and the backward pass the transposed ones, so a
-// lane's operands are contiguous in shared memory.  The group exchanges its
-// 2n values of w and y through shared memory.  y is kept in theta_out
-// between the two passes.  At t = 0, Phi_bar = Q^-1 node by node, so
-// theta = Q tau.
+// Per pair-row i, with the factor blocks pre-multiplied by the inverted
+// pivots at setup (M1 = L0^-1 L1, M2 = L0^-1 L2, N1 = L0^-T L1_{i+1}',
+// N2 = L0^-T L2_{i+2}'):
+//   forward:  y_i = L0_i^-1 tau_i - M2_i y_{i-2} - M1_i y_{i-1}
+//   backward: x_i = L0_i^-T y_i - N2_i x_{i+2} - N1_i x_{i+1}
+// Each lane computes one row of every block product, from row-major blocks,
+// so a lane's operands are contiguous in shared memory.  The three products
+// are independent: only the last one waits for the previous pair-row's
+// result, which keeps the dependent chain of a step at 2n multiply-adds.
+// The group exchanges its 2n values of tau (or y) and of the result through
+// shared memory.  y is kept in theta_out between the two passes.  At t = 0,
+// Phi_bar = Q^-1 node by node, so theta = Q tau.
 #pragma once
 
 #include <string.h>
@@ -128,9 +131,10 @@ struct SweepSmem {
   VT fac[NB][2][3 * Geo::BS];         // [buffer][class][3 blocks]
   VT halo[NB][Geo::NH][Geo::HW][NS];  // [buffer][h][t window][k]
   VT blk[NB][2][10][NS * NS];         // [buffer][jj][block][n x n]
-  VT xw[Geo::TT][Geo::G2];            // per group: w of the current pair-row
-  VT xy[Geo::TT][Geo::G2];            // per group: y or x of the current pair-row
-  double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]
+  VT xw[Geo::TT][Geo::G2];            // per group: right-hand side (tau or y) of the current step
+  VT xy[Geo::TT][Geo::G2];            // per group: result (y or x) of the current step
+  double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]; backward: r, y
+  VT ys[NB][2][NS][Geo::TT];          // backward: forward result y of the pair-row
 };
 
 // Register budget of the sweeps: one CTA per SM fewer than the shared-memory
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
 
   // ---- staging of the forward step for pair-row i into buffer b
   auto stage_forward = [&](int i, int b) {
-    // row-major L2, L1, L0^-1 (record blocks 3..5) of pair-row i, per class
+    // M2, M1, L0^-1 (record blocks 3..5) of pair-row i, per class
     for (int e = tid * CH; e < ncls * 3 * BS; e += THR * CH) {
       const int c = e / (3 * BS), off = e % (3 * BS);
       cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + 3 * BS + off);
@@ -309,16 +313,25 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
     }
   };
 
-  // ---- staging of the backward step for pair-row i: the transposed L0^-1
-  // of i, L1 of i+1 and L2 of i+2 (record blocks 2, 1, 0)
+  // ---- staging of the backward step for pair-row i: N2, N1 and L0^-T of
+  // pair-row i (record blocks 0..2), the forward result y_i of the tile
+  // (kept in theta_out between the passes; written by this CTA before the
+  // barrier that ends the forward pass), and in the mu sweep r (and y of
+  // Algorithm 1 for the flexible ratio) of the tile
+  constexpr int NVB = MU ? (FLEX ? 3 : 2) : 1;
   auto stage_backward = [&](int i, int b) {
     for (int e = tid * CH; e < ncls * 3 * BS; e += THR * CH) {
       const int c = e / (3 * BS), off = e % (3 * BS);
-      const int part = off / BS, in = off % BS;
-      const int row = i + part;
-      if (row >= g.K) continue;
-      cp_async_16(&sm.fac[b][c][off],
-                  fac_pair + (size_t)c * pd.fac_vc + (size_t)row * pd.fac_rec + (2 - part) * BS + in);
+      cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + off);
+    }
+    const long long rb = (long long)i * row_stride;
+    for (int e = tid; e < NVB * 2 * NS * TT; e += THR) {
+      const int vv = e / (2 * NS * TT), cjj = (e / (NS * TT)) % 2, kk = (e / TT) % NS, gg = e % TT;
+      const int tt = t0 + gg;
+      if (tt > g.T || (cjj == 1 && !two_cols)) continue;
+      const long long go = kk * g.Ps + rb + (long long)(j0 + cjj) * Tp + tt;
+      if (vv == 0) cp_async_elem(&sm.ys[b][cjj][kk][gg], (const VT*)a.theta_out + go);
+      else cp_async_8(&sm.src[b][vv - 1][cjj][kk][gg], (vv == 1 ? a.r : a.y) + go);
     }
   };
 
@@ -419,28 +432,30 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
         if (flex_dot) acc1 += (double)out * a.y[kP + off];
       }
     } else {
-      const VT* rec = sm.fac[b][my_slot];  // [L2][L1][L0^-1], row-major
-      VT w = tau;
-      if (i >= 1) {
-        VT row[G2];
-        lds_run<VT, G2>(rec + BS + ac * G2, row);
+      // y_i = L0^-1 tau_i - M2 y_{i-2} - M1 y_{i-1}, one chain of
+      // multiply-adds (the FP64 pipe's issue rate, not its latency, bounds
+      // the sweep, so no partial sums are split off)
+      const VT* rec = sm.fac[b][my_slot];  // [M2][M1][L0^-1], row-major
+      if (lane_ok) sm.xw[grp][al] = tau;
+      __syncwarp(gmask);
+      VT tall[G2], row0[G2];
+      lds_run<VT, G2>(&sm.xw[grp][0], tall);
+      lds_run<VT, G2>(rec + 2 * BS + ac * G2, row0);
+      VT yv = VT(0);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * ym1[bb];
-      }
+      for (int bb = 0; bb < G2; ++bb) yv += row0[bb] * tall[bb];
       if (i >= 2) {
         VT row[G2];
         lds_run<VT, G2>(rec + ac * G2, row);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * ym2[bb];
+        for (int bb = 0; bb < G2; ++bb) yv -= row[bb] * ym2[bb];
       }
-      if (lane_ok) sm.xw[grp][al] = w;
-      __syncwarp(gmask);
-      VT wall[G2], row[G2];
-      lds_run<VT, G2>(&sm.xw[grp][0], wall);
-      lds_run<VT, G2>(rec + 2 * BS + ac * G2, row);
-      VT yv = VT(0);
+      if (i >= 1) {
+        VT row[G2];
+        lds_run<VT, G2>(rec + BS + ac * G2, row);
 #pragma unroll
-      for (int bb = 0; bb < G2; ++bb) yv += row[bb] * wall[bb];
+        for (int bb = 0; bb < G2; ++bb) yv -= row[bb] * ym1[bb];
+      }
       if (node_ok) a.theta_out[kP + off] = yv;
       if (lane_ok) sm.xy[grp][al] = yv;
       __syncwarp(gmask);
@@ -465,40 +480,40 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
     const int b = step % NB;
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
-    VT yown = VT(0);
-    double r_own = 0.0, y_own = 0.0;
-    if (t >= 1 && node_ok) {
-      yown = a.theta_out[kP + off];
-      if (MU) r_own = a.r[kP + off];
-      if (flex_dot) y_own = a.y[kP + off];
-    }
     cp_async_wait<1>();
     __syncthreads();
     if (i >= 2) stage_backward(i - 2, (step + 2) % NB);
     cp_async_commit();
+    VT yown = VT(0);
+    double r_own = 0.0, y_own = 0.0;
+    if (t >= 1 && node_ok) {
+      yown = sm.ys[b][jj][k][grp];
+      if (MU) r_own = sm.src[b][0][jj][k][grp];
+      if (flex_dot) y_own = sm.src[b][1][jj][k][grp];
+    }
     if (t >= 1) {
-      const VT* rec = sm.fac[b][my_slot];  // [L0^-1'(i)][L1'(i+1)][L2'(i+2)]: row a = column a of L
-      VT w = yown;
+      // x_i = L0^-T y_i - N2 x_{i+2} - N1 x_{i+1}
+      const VT* rec = sm.fac[b][my_slot];  // [N2][N1][L0^-T], row-major
+      if (lane_ok) sm.xw[grp][al] = yown;
+      __syncwarp(gmask);
+      VT yall[G2], row0[G2];
+      lds_run<VT, G2>(&sm.xw[grp][0], yall);
+      lds_run<VT, G2>(rec + 2 * BS + ac * G2, row0);
+      VT xv = VT(0);
+#pragma unroll
+      for (int bb = 0; bb < G2; ++bb) xv += row0[bb] * yall[bb];
+      if (i + 2 < g.K) {
+        VT row[G2];
+        lds_run<VT, G2>(rec + ac * G2, row);
+#pragma unroll
+        for (int bb = 0; bb < G2; ++bb) xv -= row[bb] * xp2[bb];
+      }
       if (i + 1 < g.K) {
         VT row[G2];
         lds_run<VT, G2>(rec + BS + ac * G2, row);
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * xp1[bb];
+        for (int bb = 0; bb < G2; ++bb) xv -= row[bb] * xp1[bb];
       }
-      if (i + 2 < g.K) {
-        VT row[G2];
-        lds_run<VT, G2>(rec + 2 * BS + ac * G2, row);
-#pragma unroll
-        for (int bb = 0; bb < G2; ++bb) w -= row[bb] * xp2[bb];
-      }
-      if (lane_ok) sm.xw[grp][al] = w;
-      __syncwarp(gmask);
-      VT wall[G2], row[G2];
-      lds_run<VT, G2>(&sm.xw[grp][0], wall);
-      lds_run<VT, G2>(rec + ac * G2, row);
-      VT xv = VT(0);
-#pragma unroll
-      for (int bb = 0; bb < G2; ++bb) xv += row[bb] * wall[bb];
       if (node_ok) {
         a.theta_out[kP + off] = xv;
         if (MU) acc0 += (double)xv * r_own;
