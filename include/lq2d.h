@@ -101,6 +101,8 @@ typedef struct lq2d_stats {
   double kappa_estimate;   /* lambda_max / lambda_min (LQ2D_OPT_KAPPA), else 0 */
   double lambda_min;       /* extreme Ritz values of the preconditioned operator */
   double lambda_max;
+  int sweep_threads;       /* threads per CTA of the current precision mode's sweeps */
+  int pad2;
 } lq2d_stats;
 
 /* Creates a problem from host arrays, copies them to the current device and
@@ -190,9 +192,9 @@ int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const v
 /* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS) for this problem's shape
  * and the handle's current precision mode by timing: runs D_S (S outer x L
  * inner sweeps, Algorithm 2) once as warm-up and then `reps` times with each
- * candidate width (32, 64, 128, 256), with CUDA events on `stream`, and keeps the
- * faster for later solves of this precision mode (FP64 and FP32 sweeps keep
- * separate choices).  The problem's right-hand side is the input; the
+ * candidate width (32, 64, 128, 256), with CUDA events on `stream`, and keeps
+ * the fastest for later solves of this precision mode (FP64 and FP32 sweeps
+ * keep separate choices).  The problem's right-hand side is the input; the
  * handle's solution buffers are not touched.
  *   threads (out, may be NULL): the chosen width
  *   ms      (out, may be NULL): its time per D_S application, milliseconds

@@ -1309,6 +1309,7 @@ int lq2d_get_stats(const lq2d_problem* h, lq2d_stats* out) {
   if (!h || !out) return fail(LQ2D_EINVAL, "null argument");
   *out = h->stats;
   out->launches_total = h->launches;
+  out->sweep_threads = h->sweep_threads[h->precision >= 1 ? 1 : 0];
   return LQ2D_OK;
 }
 

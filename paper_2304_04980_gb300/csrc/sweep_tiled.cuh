@@ -6,9 +6,9 @@
 // consecutive time steps; a group of GS lanes solves one (v, t) block, lane
 // a owning unknown a = jj*NS + k of every pair-row (node (i, 2v+jj),
 // component k).  All groups of a CTA walk the K pair-rows together.  For
-// pair-row i+2 the CTA copies into shared memory, with cp.async while
-// pair-row i is computed (three buffers):
-//   * the factor blocks of pair-row i+2 (both time classes when the tile
+// pair-row i+PD the CTA copies into shared memory, with cp.async while
+// pair-row i is computed (PD + 1 buffers, PD = 2):
+//   * the factor blocks of pair-row i+PD (both time classes when the tile
 //     holds t = T), read by every group of the tile;
 //   * the pair-row's own entries for the TT steps (the right-hand side, or
 //     r, y, d, delta in the sweep that performs the PCG update);
@@ -45,8 +45,14 @@ struct SweepGeom {
   static constexpr int TT = THR / GS;            // time steps per CTA
   static constexpr int NH = 8;                   // staged neighbour nodes per pair-row
   static constexpr int HW = TT + 2;              // staged time window (t0-1 .. t0+TT)
-  static constexpr int NB = 3;                   // pipeline depth (buffers)
 };
+
+// Pipeline depth (staging buffers; pair-rows in flight = NB - 1).  Two
+// pair-rows in flight cover the load latency in both precisions: six
+// buffers timed no faster in FP32 on the 64 x 64 x 100 grid and slower on
+// the 256 x 256 x 200 grid (fewer CTAs per SM).
+template <typename VT>
+__host__ __device__ constexpr int sweep_stages() { return 3; }
 
 __device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -127,7 +133,7 @@ __device__ __forceinline__ int h_of_dir(int jj, int dir) {
 template <int NS, typename VT, int THR>
 struct SweepSmem {
   using Geo = SweepGeom<NS, THR>;
-  static constexpr int NB = Geo::NB;
+  static constexpr int NB = sweep_stages<VT>();
   VT fac[NB][2][3 * Geo::BS];         // [buffer][class][3 blocks]
   VT halo[NB][Geo::NH][Geo::HW][NS];  // [buffer][h][t window][k]
   VT blk[NB][2][10][NS * NS];         // [buffer][jj][block][n x n]
@@ -135,6 +141,7 @@ struct SweepSmem {
   VT xy[Geo::TT][Geo::G2];            // per group: result (y or x) of the current step
   double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]; backward: r, y
   VT ys[NB][2][NS][Geo::TT];          // backward: forward result y of the pair-row
+  alignas(16) VT qb[NB][2][NS * NS];  // Q of the pair-row's nodes (tiles holding t = 0)
 };
 
 // Register budget of the sweeps: one CTA per SM fewer than the shared-memory
@@ -282,6 +289,14 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       const int c = e / (3 * BS), off = e % (3 * BS);
       cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + 3 * BS + off);
     }
+    if (t0 == 0) {
+      // Q of the pair-row's nodes, for theta = Q tau at t = 0
+      for (int e = tid; e < 2 * NS * NS; e += THR) {
+        const int cjj = e / (NS * NS), w = e % (NS * NS);
+        if (cjj == 1 && !two_cols) continue;
+        cp_async_elem(&sm.qb[b][cjj][w], pd.Qm + (size_t)(i * g.N + j0 + cjj) * NS * NS + w);
+      }
+    }
     const long long rb = (long long)i * row_stride;
 #pragma unroll
     for (int sl = 0; sl < SSL; ++sl) {
@@ -339,20 +354,25 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
 #pragma unroll
   for (int bb = 0; bb < G2; ++bb) { ym1[bb] = VT(0); ym2[bb] = VT(0); }
 
-  constexpr int NB = Geo::NB;
-  stage_forward(0, 0);
-  cp_async_commit();
-  if (g.K > 1) stage_forward(1, 1);
-  cp_async_commit();
+  constexpr int NB = sweep_stages<VT>();
+  constexpr int PD = NB - 1;  // prefetch distance in pair-rows
+  // one commit group per pair-row (empty past the last one), so that the
+  // wait below counts pair-rows
+#pragma unroll
+  for (int s0 = 0; s0 < PD; ++s0) {
+    if (s0 < g.K) stage_forward(s0, s0);
+    cp_async_commit();
+  }
   for (int i = 0; i < g.K; ++i) {
     const int b = i % NB;
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
-    // pair-row i has landed (only i+1 may be in flight); after the barrier
-    // every thread is done with step i-1, whose buffer takes pair-row i+2
-    cp_async_wait<1>();
+    // pair-row i has landed (rows i+1 .. i+PD-1 may be in flight); after the
+    // barrier every thread is done with step i-1, whose buffer takes
+    // pair-row i+PD
+    cp_async_wait<PD - 1>();
     __syncthreads();
-    if (i + 2 < g.K) stage_forward(i + 2, (i + 2) % NB);
+    if (i + PD < g.K) stage_forward(i + PD, (i + PD) % NB);
     cp_async_commit();
     const unsigned valid = HALO ? row_valid(i) : 0u;
     VT tau = VT(0);
@@ -418,19 +438,18 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       }
     }
     if (t == 0) {
-      // Phi_bar_{v,0} = blkdiag(Q^-1): theta = Q tau, node by node
+      // Phi_bar_{v,0} = blkdiag(Q^-1): theta = Q tau, node by node (Q rows
+      // staged with the pair-row; the mu terms of t = 0 are added in the
+      // backward pass, where r and y of the tile are staged)
       VT out = VT(0);
-      const VT* Qrow = pd.Qm + ((size_t)p * NS + k) * NS;
+      VT Qrow[NS];
+      lds_run<VT, NS>(&sm.qb[b][jj][k * NS], Qrow);
 #pragma unroll
       for (int c = 0; c < NS; ++c) {
         const VT tc = __shfl_sync(gmask, tau, jj * NS + c, GS);
-        if (node_ok) out += Qrow[c] * tc;
+        out += Qrow[c] * tc;
       }
-      if (node_ok) {
-        a.theta_out[kP + off] = out;
-        if (MU) acc0 += (double)out * a.r[kP + off];
-        if (flex_dot) acc1 += (double)out * a.y[kP + off];
-      }
+      if (node_ok) a.theta_out[kP + off] = out;
     } else {
       // y_i = L0^-1 tau_i - M2 y_{i-2} - M1 y_{i-1}, one chain of
       // multiply-adds (the FP64 pipe's issue rate, not its latency, bounds
@@ -471,25 +490,31 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   VT xp1[G2], xp2[G2];
 #pragma unroll
   for (int bb = 0; bb < G2; ++bb) { xp1[bb] = VT(0); xp2[bb] = VT(0); }
-  stage_backward(g.K - 1, 0);
-  cp_async_commit();
-  if (g.K > 1) stage_backward(g.K - 2, 1);
-  cp_async_commit();
+#pragma unroll
+  for (int s0 = 0; s0 < PD; ++s0) {
+    if (s0 < g.K) stage_backward(g.K - 1 - s0, s0);
+    cp_async_commit();
+  }
   for (int i = g.K - 1; i >= 0; --i) {
     const int step = g.K - 1 - i;
     const int b = step % NB;
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
-    cp_async_wait<1>();
+    cp_async_wait<PD - 1>();
     __syncthreads();
-    if (i >= 2) stage_backward(i - 2, (step + 2) % NB);
+    if (i >= PD) stage_backward(i - PD, (step + PD) % NB);
     cp_async_commit();
     VT yown = VT(0);
     double r_own = 0.0, y_own = 0.0;
-    if (t >= 1 && node_ok) {
+    if (node_ok) {
       yown = sm.ys[b][jj][k][grp];
       if (MU) r_own = sm.src[b][0][jj][k][grp];
       if (flex_dot) y_own = sm.src[b][1][jj][k][grp];
+      if (t == 0) {
+        // theta_0 = Q tau_0 is final after the forward pass
+        if (MU) acc0 += (double)yown * r_own;
+        if (flex_dot) acc1 += (double)yown * y_own;
+      }
     }
     if (t >= 1) {
       // x_i = L0^-T y_i - N2 x_{i+2} - N1 x_{i+1}

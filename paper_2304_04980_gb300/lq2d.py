@@ -45,6 +45,7 @@ class Stats(ctypes.Structure):
         ("launches_total", ctypes.c_longlong), ("body_executions", ctypes.c_int),
         ("outer_iterations", ctypes.c_int), ("kappa_estimate", ctypes.c_double),
         ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
+        ("sweep_threads", ctypes.c_int), ("pad2", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -247,7 +248,7 @@ class Problem:
 
     def autotune(self, S=2, L=2, reps=5, stream=None):
         """Times the sweep tile widths for this shape and precision mode and
-        keeps the faster; returns (threads, ms per preconditioner apply)."""
+        keeps the fastest; returns (threads, ms per preconditioner apply)."""
         thr, ms = ctypes.c_int(0), ctypes.c_double(0.0)
         _check(load().lq2d_autotune(self._h, S, L, reps, ctypes.byref(thr), ctypes.byref(ms), _stream(stream)))
         return thr.value, ms.value

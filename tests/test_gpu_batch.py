@@ -122,6 +122,7 @@ def test_sweep_widths_match_oracle(dev, shape, mode):
         q = torch.empty_like(rt)
         prob.apply_precond_device(2, 2, rt, q)
         assert np.abs(q.cpu().numpy().ravel() - ref).max() <= bound, thr
+        assert prob.stats()["sweep_threads"] == thr
 
 
 def test_autotune_picks_a_width_and_keeps_results(dev):
@@ -131,6 +132,7 @@ def test_autotune_picks_a_width_and_keeps_results(dev):
     base = prob.solve(1e-10, 2, 2, 5000)
     thr, ms = prob.autotune(2, 2, 3)
     assert thr in (32, 64, 128, 256) and ms > 0
+    assert prob.stats()["sweep_threads"] == thr
     out = prob.solve(1e-10, 2, 2, 5000)
     assert out["status"] == 0
     assert np.linalg.norm(out["costate"] - base["costate"]) <= 1e-8 * np.linalg.norm(base["costate"])

@@ -47,9 +47,26 @@ def test_status_codes_match_header():
     assert int(codes["ENOTPD"]) == lq2d.ENOTPD and int(codes["ETIMEOUT"]) == lq2d.ETIMEOUT
 
 
-def test_stats_struct_layout():
+def test_stats_struct_layout(tmp_path):
+    """The binding's Stats mirrors lq2d_stats of include/lq2d.h: a C program
+    compiled against the header prints the size and every field offset."""
+    import shutil
+    import subprocess
     from paper_2304_04980_gb300 import lq2d
-    assert ctypes.sizeof(lq2d.Stats) == 6 * 4 + 6 * 8 + 8 + 2 * 4 + 3 * 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [n for n, _ in lq2d.Stats._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lq2d.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(lq2d_stats));\n' +
+                   "".join('  printf("%%zu\\n", offsetof(lq2d_stats, %s));\n' % n for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(lq2d.Stats)
+    assert out[1:] == [getattr(lq2d.Stats, n).offset for n in names]
 
 
 @pytest.mark.parametrize("dims", [(0, 4, 4, 2, 1), (4, 0, 4, 2, 1), (4, 4, 0, 2, 1), (4, 4, 4, 0, 1),
