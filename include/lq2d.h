@@ -84,7 +84,7 @@ enum {
 /* Statistics of the last solve on a handle. */
 typedef struct lq2d_stats {
   int iterations;          /* PCG steps (loop passes of Algorithm 1) over all restarts */
-  int restarts;            /* restarts from the true residual */
+  int restarts;            /* restarts from the true residual (direction reset) */
   int status;              /* status returned by the solve */
   int sweep_launches;      /* timed sweep launches (timing option) */
   int delta_launches;      /* timed Delta-apply launches (timing option, 2 kernels each) */
@@ -102,7 +102,7 @@ typedef struct lq2d_stats {
   double lambda_min;       /* extreme Ritz values of the preconditioned operator */
   double lambda_max;
   int sweep_threads;       /* threads per CTA of the current precision mode's sweeps */
-  int pad2;
+  int residual_replacements; /* precision mode 2: recurrence residuals replaced by the true one */
 } lq2d_stats;
 
 /* Creates a problem from host arrays, copies them to the current device and
@@ -263,11 +263,13 @@ int lq2d_get_stats(const lq2d_problem *h, lq2d_stats *out);
  *      FP64 residual.
  *   2: as 1, and the product Delta d inside the Krylov loop in FP32 too.
  *      The recurrence residual then drifts from the true one at FP32 level,
- *      so the loop runs in phases: a phase ends when the recurrence
- *      residual has dropped by 1e4 (or meets the tolerance), the residual is
- *      recomputed in FP64 from the iterate and the iteration restarts from
- *      it (reliable residual replacement).  Residual recomputation, the
- *      direction update and every dot product stay FP64.
+ *      so whenever it has dropped by 1e4 since the last replacement, the
+ *      residual is recomputed in FP64 from the iterate, r = r_delta -
+ *      Delta delta, and replaces it on the device; the search direction is
+ *      kept, so the iteration continues without a restart (a reliable
+ *      update; lq2d_stats.residual_replacements counts them).  Residual
+ *      recomputation, the direction update and every dot product stay FP64;
+ *      the stop test is confirmed on the true residual at exit.
  * Modes 1 and 2 allocate FP32 copies of the operands on first use and
  * refresh them at every setup. */
 int lq2d_set_precision(lq2d_problem *h, int mode);

@@ -38,7 +38,11 @@ struct SolverState {
   unsigned int counters[8];  // arrival counters of the last-block reductions
   double* hist;       // optional: vartheta_j at [2j], beta_j at [2j+1] (Lanczos estimate), or NULL
   double tol_bound;   // the tolerance itself, in the units of stop_bound
-  double phase_rho2;  // > 0: a phase also ends once ||r||^2 <= phase_rho2 ||r_start||^2 (precision mode 2)
+  double phase_rho2;  // > 0 (precision mode 2): replace the recurrence residual by the true one once
+                      // ||r||^2 <= phase_rho2 ||r_ref||^2
+  double rref2;       // ||r||^2 at the start or at the last replacement
+  int replace;        // set by the step whose residual met the replacement test; cleared by the replacement
+  int replacements;   // residual replacements in this solve
 };
 
 // Records the PCG coefficients of step j (called by the last block of the
@@ -51,7 +55,7 @@ __device__ inline void record_beta(SolverState* st, int j) {
 }
 
 enum StateDone { kRunning = 0, kConverged = 1, kMaxIter = 2, kBreakdown = 3, kLoopCap = 4 };
-enum CounterSlot { kCntDot = 0, kCntNorm = 1, kCntMu = 2, kCntInit = 3, kCntKkt = 4, kCntAux = 5 };
+enum CounterSlot { kCntDot = 0, kCntNorm = 1, kCntMu = 2, kCntInit = 3, kCntKkt = 4, kCntAux = 5, kCntRepl = 6 };
 
 struct Grid {
   int K, N, T, n, m, V, NN;

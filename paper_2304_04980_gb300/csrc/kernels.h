@@ -126,6 +126,10 @@ void launch_nbjm_diff(const Grid& g, const void* a, const void* b, int fp32, dou
                       cudaStream_t s);
 void launch_init_residual(const Grid& g, const double* rhs, const double* y, double* r, double* delta,
                           const double* delta0, double* partials, SolverState* st, cudaStream_t s);
+// reliable update of precision mode 2: r = rhs - y when the state asks for a
+// replacement (y = Delta delta from the gated Delta kernels), else nothing
+void launch_replace_residual(const Grid& g, const double* rhs, const double* y, double* r, double* partials,
+                             SolverState* st, cudaStream_t s);
 void launch_norms(const Grid& g, const double* v, int comps, double* partials, unsigned int* counter,
                   double* out2, cudaStream_t s);
 void launch_build_rhs(const Grid& g, const double* x0, const double* w_api, double* rhs, cudaStream_t s);

@@ -30,14 +30,17 @@ __device__ __forceinline__ auto ahat_col(const D& nd, int r, int dir) {
 //   z_t = Q_t^-1 (A~' dn)_t                 (Q_T at t = T)
 // dn = q + beta d_old is formed on the fly (the direction update of
 // Algorithm 1 fused into its operator product); beta comes from the device
-// state.
+// state.  use_beta: 0 plain, 1 with the direction update (skipped once the
+// loop has stopped), 2 plain but only when the state asks for a residual
+// replacement (the reliable update of precision mode 2).
 // ---------------------------------------------------------------------------
 template <int NS, typename QT, typename CT, typename DT>
 __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> nd, const QT* __restrict__ q,
                                                              const DT* __restrict__ dold,
                                                              CT* __restrict__ z,
                                                              const SolverState* __restrict__ st, int use_beta) {
-  if (use_beta && st->done) return;
+  if (use_beta == 1 && st->done) return;
+  if (use_beta == 2 && (st->done || !st->replace)) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.P) return;
   const int Tp = g.T + 1;
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
   const int i = p / g.N, j = p % g.N;
   // dn = q + beta d_old is formed in the precision of d_old (FP64, or FP32
   // when the FP32 copy of d is read)
-  const DT beta = use_beta ? (DT)st->beta : DT(0);
+  const DT beta = use_beta == 1 ? (DT)st->beta : DT(0);
   const bool mix = beta != DT(0);
   CT w[NS];
 #pragma unroll
@@ -89,6 +92,8 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
 //   y_0 = -z_0,   y_t = A_hat z_{t-1} - z_t + S dn_t   (t >= 1, S = B R^-1 B')
 // Loop mode (Algorithm 1: operator product, step length, direction update): dn = q + beta d_old is written back
 // to d (each thread owns its entry), y' dn is reduced and vartheta set.
+// Plain mode with a state: runs only when the state asks for a residual
+// replacement (the reliable update of precision mode 2).
 // ---------------------------------------------------------------------------
 template <int NS, bool LOOP, typename QT, typename CT>
 __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> nd, const CT* __restrict__ z,
@@ -98,6 +103,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> 
                                                              double* __restrict__ y, double* __restrict__ partials,
                                                              SolverState* st) {
   if (LOOP && st->done) return;
+  if (!LOOP && st != nullptr && (st->done || !st->replace)) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (idx < g.P) {

@@ -41,7 +41,11 @@ __global__ void init_state_kernel(SolverState* st, double tol, int max_iter, int
   st->stop_bound = stop_mode == 0 ? tol * tol * st->bnorm2 : tol;
   st->tol_bound = st->stop_bound;
   st->phase_rho2 = stop_mode == 0 ? phase_rho2 : 0.0;
-  if (!keep_iter) st->iter = 0;
+  st->replace = 0;
+  if (!keep_iter) {
+    st->iter = 0;
+    st->replacements = 0;
+  }
   st->max_iter = max_iter;
   st->done = 0;
   st->have_mu = 0;
@@ -151,12 +155,40 @@ __global__ void init_residual_kernel(Grid g, const double* __restrict__ rhs, con
     st->rnorm2 = t0;
     st->rnorm_inf = t1;
     const bool pass = st->stop_mode == 0 ? (t0 <= st->tol_bound) : (t1 < st->tol_bound);
-    // a phase of precision mode 2 ends once the recurrence residual has
-    // dropped by sqrt(phase_rho2) (or meets the tolerance)
-    if (st->phase_rho2 > 0.0) st->stop_bound = fmax(st->tol_bound, st->phase_rho2 * t0);
+    st->rref2 = t0;
     if (!isfinite(t0)) st->done = kBreakdown;
     else if (pass) st->done = kConverged;
     else if (st->iter >= st->max_iter) st->done = kMaxIter;
+  }
+}
+
+// Reliable update of precision mode 2 (Krylov products in FP32): when the
+// step just taken set the replacement flag, r = r_delta - Delta delta with
+// Delta delta computed in FP64 (y, by the two gated Delta kernels before
+// this one) replaces the recurrence residual; the search direction d is
+// kept, so the iteration continues instead of restarting.
+__global__ void replace_residual_kernel(Grid g, const double* __restrict__ rhs, const double* __restrict__ y,
+                                        double* __restrict__ r, double* partials, SolverState* st) {
+  if (st->done || !st->replace) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double s2 = 0.0, mx = 0.0;
+  if (idx < g.P) {
+    for (int k = 0; k < g.n; ++k) {
+      const long long e = k * g.Ps + idx;
+      const double rv = rhs[e] - y[e];
+      r[e] = rv;
+      s2 += rv * rv;
+      mx = fmax(mx, fabs(rv));
+    }
+  }
+  double t0, t1;
+  if (grid_reduce2<true>(s2, mx, partials, &st->counters[kCntRepl], &t0, &t1)) {
+    st->rnorm2 = t0;
+    st->rnorm_inf = t1;
+    st->rref2 = t0;
+    st->replace = 0;
+    st->replacements += 1;
+    if (!isfinite(t0)) st->done = kBreakdown;
   }
 }
 
@@ -281,6 +313,11 @@ void launch_nbjm_diff(const Grid& g, const void* a, const void* b, int fp32, dou
 void launch_init_residual(const Grid& g, const double* rhs, const double* y, double* r, double* delta,
                           const double* delta0, double* partials, SolverState* st, cudaStream_t s) {
   init_residual_kernel<<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, rhs, y, r, delta, delta0, partials, st);
+}
+
+void launch_replace_residual(const Grid& g, const double* rhs, const double* y, double* r, double* partials,
+                             SolverState* st, cudaStream_t s) {
+  replace_residual_kernel<<<blocks_for(g.P, kOpThreads), kOpThreads, 0, s>>>(g, rhs, y, r, partials, st);
 }
 
 void launch_norms(const Grid& g, const double* v, int comps, double* partials, unsigned int* counter,

@@ -38,11 +38,10 @@ struct GraphEntry {
 
 constexpr int kMaxGraphs = 8;
 constexpr int kHistCap = 1 << 16;  // PCG steps whose coefficients are kept for the Lanczos estimate
-// Precision mode 2: a phase of the FP32-product Krylov loop ends once the
-// recurrence residual has dropped by kPhaseRho; the FP64 true residual then
-// replaces it (at most kPhaseRestarts times).
+// Precision mode 2: once the recurrence residual of the FP32-product Krylov
+// loop has dropped by kPhaseRho since the last replacement, the FP64 true
+// residual replaces it and the iteration continues with the same direction.
 constexpr double kPhaseRho = 1e-4;
-constexpr int kPhaseRestarts = 40;
 constexpr int kStreamChunk = 4;  // steps enqueued between stop-flag reads (driver 1)
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
@@ -445,6 +444,16 @@ void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
     return;
   }
   enqueue_precond(h, S, L, true, true, h->st, h->r, s, timing);
+  if (h->precision == 2) {
+    // reliable update: when this step's residual has dropped by kPhaseRho
+    // since the last replacement, r = r_delta - Delta delta in FP64 replaces
+    // the recurrence residual (the three kernels return at once otherwise);
+    // d, q and mu of the step are kept
+    h->kt->delta_z(h->g, h->op64, h->delta, nullptr, h->z, h->st, 2, s);
+    h->kt->delta_y(h->g, h->op64, h->z, h->delta, nullptr, nullptr, h->y, h->partials, h->st, 0, s);
+    launch_replace_residual(h->g, h->rhs, h->y, h->r, h->partials, h->st, s);
+    h->launches += 3;
+  }
 }
 
 // CTA width of the sweeps the current precision mode launches.
@@ -650,7 +659,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     if (rc) return rc;
   }
   const double phase_rho2 = h->precision == 2 ? kPhaseRho * kPhaseRho : 0.0;
-  const int max_restarts = h->precision == 2 ? std::max(h->max_restarts, kPhaseRestarts) : h->max_restarts;
+  const int max_restarts = h->max_restarts;
   launch_init_state(h->st, tol, max_iter, h->stop_mode, h->bnorm, 0, h->kappa ? h->hist : nullptr, kHistCap,
                     phase_rho2, s);
   h->launches += 2;  // state and initial residual
@@ -715,6 +724,7 @@ int solve_impl(lq2d_problem* h, double tol, int S, int L, int max_iter, const do
     }
     h->stats.iterations = hs.iter;
     h->stats.restarts = restarts;
+    h->stats.residual_replacements = hs.replacements;
     h->stats.rel_residual = bn > 0 ? std::sqrt(hs.rnorm2) / bn : std::sqrt(hs.rnorm2);
     h->stats.rel_kkt_residual = rel;
     h->stats.kkt_inf = h->h_kkt[2];

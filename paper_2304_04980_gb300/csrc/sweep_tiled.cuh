@@ -566,6 +566,8 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       if (!isfinite(tot0)) st->done = kBreakdown;
       else if (pass) st->done = kConverged;
       else if (it >= st->max_iter) st->done = kMaxIter;
+      // precision mode 2: the residual is due for replacement by the true one
+      if (!st->done && st->phase_rho2 > 0.0 && tot0 <= st->phase_rho2 * st->rref2) st->replace = 1;
     }
   }
   if (MU) {

@@ -45,7 +45,7 @@ class Stats(ctypes.Structure):
         ("launches_total", ctypes.c_longlong), ("body_executions", ctypes.c_int),
         ("outer_iterations", ctypes.c_int), ("kappa_estimate", ctypes.c_double),
         ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
-        ("sweep_threads", ctypes.c_int), ("pad2", ctypes.c_int),
+        ("sweep_threads", ctypes.c_int), ("residual_replacements", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -89,10 +89,11 @@ def test_mixed_solve_matches_oracle(dev, shape, mode):
         # FP32 rounding inside the preconditioner costs at most a few iterations
         assert out["iterations"] <= int(1.25 * plain["iterations"]) + 3
     else:
-        # the FP32 product restarts the recurrences once per phase of 1e4
+        # the FP32 product's residual is replaced by the FP64 one once per
+        # drop of 1e4, keeping the direction: no restart, few extra steps
         st = prob.stats()
-        assert st["restarts"] >= 1
-        assert out["iterations"] <= 2 * plain["iterations"] + 10
+        assert st["residual_replacements"] >= 1
+        assert out["iterations"] <= int(1.5 * plain["iterations"]) + 5
 
 
 def test_mode_switch_and_update_refresh_fp32_operands(dev):
