@@ -189,6 +189,26 @@ int lq2d_apply_delta_device(lq2d_problem *h, const void *d_in, void *d_out, void
 int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const void *d_r,
                               void *d_q, void *stream);
 
+/* q_r = D_S r_r for up to 32 right-hand sides r_r of one problem at once
+ * (Algorithm 2, S outer x L inner sweeps from zero starts; Theorem
+ * posdef_preconditioner), the right-hand sides sharing Delta, its splittings
+ * and the banded factors of Phi_bar (Section IV-B).  Every sweep step
+ * applies each 2n x 2n factor block and the pair-row's coupling to the
+ * neighbouring nodes to all 32 right-hand sides as one matrix product on
+ * the tensor cores: TF32 operands (10-bit mantissa) with FP32
+ * accumulation, FP32 iterates.  The result is therefore D_S r only to about
+ * 1e-3 relative, enough for a preconditioner.
+ *   nrhs       1..32
+ *   d_r, d_q   device buffers [nrhs][T+1][K*N][n] (FP64), right-hand side
+ *              r of index i at d_r + i (T+1) K N n
+ * Needs n = 4 (LQ2D_EINVAL otherwise).  The first call allocates the
+ * operands of this path (about 16 (T+1) K N n bytes per vector, four
+ * vectors, plus the rearranged factors) and every setup invalidates them;
+ * they are rebuilt on the next call.  Returns after the work on `stream`
+ * is complete. */
+int lq2d_apply_precond_multi_device(lq2d_problem *h, int nrhs, int outer_S, int inner_L, const void *d_r,
+                                    void *d_q, void *stream);
+
 /* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS) for this problem's shape
  * and the handle's current precision mode by timing: runs D_S (S outer x L
  * inner sweeps, Algorithm 2) once as warm-up and then `reps` times with each

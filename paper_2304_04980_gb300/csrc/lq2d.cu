@@ -9,6 +9,7 @@
 
 #include "../../include/lq2d.h"
 #include "kernels.h"
+#include "mrhs.h"
 #include "setup.h"
 
 using namespace lq2d;
@@ -95,6 +96,11 @@ struct lq2d_problem {
   double* hist = nullptr;    // device: vartheta_j, beta_j pairs
   std::vector<double> h_hist;
   int graph_body_kernels = 0;  // kernels per device-loop body of the last graph launch (0: no graph)
+  // multi-right-hand-side preconditioner (n = 4; allocated on first use,
+  // rebuilt after every setup)
+  mrhs::Buffers mb{};
+  float *m_src = nullptr, *m_thA = nullptr, *m_thB = nullptr, *m_rth = nullptr;
+  bool mrhs_built = false;
 };
 
 // Many problems solved by one graph launch: one independent chain per
@@ -274,6 +280,7 @@ int run_setup(lq2d_problem* h, cudaStream_t s) {
   LQ_CUDA(cudaMemsetAsync(h->setup_status, 0, sizeof(int), s));
   launch_setup(h->sb, g.K, g.N, g.n, g.m, g.V, h->nd.fac_rec, h->nd.fac_vc, h->setup_status, s);
   if (h->f32_buf) convert_prec_f32(h, s);
+  h->mrhs_built = false;
   launch_build_rhs(g, h->sb.x0, h->w_aff, h->rhs, s);
   launch_norms(g, h->rhs, g.n, h->partials, &h->st->counters[kCntAux], h->bnorm, s);
   h->launches += 7;
@@ -966,6 +973,64 @@ int batch_build(lq2d_batch* b, double tol, int S, int L, int max_iter) {
   return LQ2D_OK;
 }
 
+// Float buffer of `count` elements from the handle's allocations.
+int alloc_floats(lq2d_problem* h, float** p, size_t count) {
+  double* d = nullptr;
+  const int rc = dev_alloc(h, &d, (count + 1) / 2);
+  *p = reinterpret_cast<float*>(d);
+  return rc;
+}
+
+// Multi-right-hand-side operands: allocated on first use, rebuilt from the
+// FP64 setup after every setup.
+int ensure_mrhs(lq2d_problem* h, cudaStream_t s) {
+  const Grid& g = h->g;
+  if (!h->mb.rec) {
+    LQ_CUDA(mrhs::prepare());
+    int rc;
+    if ((rc = alloc_floats(h, &h->mb.rec, (size_t)mrhs::rec_floats(g))) != LQ2D_OK) return rc;
+    if ((rc = alloc_floats(h, &h->mb.wom, (size_t)mrhs::w_floats(g))) != LQ2D_OK) return rc;
+    if ((rc = alloc_floats(h, &h->mb.wxa, (size_t)mrhs::w_floats(g))) != LQ2D_OK) return rc;
+    if ((rc = alloc_floats(h, &h->mb.wxq, (size_t)mrhs::w_floats(g))) != LQ2D_OK) return rc;
+    const size_t vec = (size_t)mrhs::vec_floats(g);
+    if ((rc = alloc_floats(h, &h->m_src, vec)) != LQ2D_OK) return rc;
+    if ((rc = alloc_floats(h, &h->m_thA, vec)) != LQ2D_OK) return rc;
+    if ((rc = alloc_floats(h, &h->m_thB, vec)) != LQ2D_OK) return rc;
+    if ((rc = alloc_floats(h, &h->m_rth, vec)) != LQ2D_OK) return rc;
+  }
+  if (!h->mrhs_built) {
+    mrhs::launch_build(g, h->nd, h->mb, s);
+    h->launches += 2;
+    h->mrhs_built = true;
+  }
+  return LQ2D_OK;
+}
+
+// q = D_S r for the 32 right-hand sides of m_src (Algorithm 2, S x L sweeps
+// from zero starts); returns the buffer holding q.
+const float* enqueue_precond_multi(lq2d_problem* h, int S, int L, cudaStream_t s) {
+  float* bufs[2] = {h->m_thA, h->m_thB};
+  int out_i = 0;
+  const float* prev = nullptr;
+  for (int so = 0; so < S; ++so) {
+    for (int l = 0; l < L; ++l) {
+      int variant;
+      const float* src = h->m_src;
+      if (l == 0 && so == 0) variant = 0;
+      else if (l == 0) variant = 2;
+      else {
+        variant = 1;
+        if (so > 0) src = h->m_rth;
+      }
+      mrhs::launch_sweep(variant, h->g, h->mb, src, prev, bufs[out_i], h->m_rth, s);
+      h->launches += 1;
+      prev = bufs[out_i];
+      out_i ^= 1;
+    }
+  }
+  return prev;
+}
+
 }  // namespace
 
 namespace lq2d {
@@ -1120,6 +1185,25 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
     qd = h->thA;
   }
   launch_to_api(qd, static_cast<double*>(d_q), g.NN, g.T + 1, g.n, g.Ps, s);
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  return LQ2D_OK;
+}
+
+int lq2d_apply_precond_multi_device(lq2d_problem* h, int nrhs, int S, int L, const void* d_r, void* d_q,
+                                    void* stream) {
+  if (!h || !d_r || !d_q) return fail(LQ2D_EINVAL, "null argument");
+  if (h->g.n != mrhs::kN) return fail(LQ2D_EINVAL, "the multi-right-hand-side path needs n = 4");
+  if (nrhs < 1 || nrhs > mrhs::kRhs) return fail(LQ2D_EINVAL, "nrhs must be in 1..32");
+  if (S < 1) return fail(LQ2D_EINVAL, "outer_S must be >= 1");
+  if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_mrhs(h, s);
+  if (rc != LQ2D_OK) return rc;
+  mrhs::launch_from_api(h->g, nrhs, static_cast<const double*>(d_r), h->m_src, s);
+  const float* q = enqueue_precond_multi(h, S, L, s);
+  mrhs::launch_to_api(h->g, nrhs, q, static_cast<double*>(d_q), s);
+  h->launches += 2;
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
   return LQ2D_OK;

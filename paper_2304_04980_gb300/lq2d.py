@@ -25,6 +25,7 @@ OPT_SWEEP_THREADS = 7
 EXPORTED = (
     "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
     "lq2d_solve_device", "lq2d_solve_nbjm_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_apply_delta_static",
+    "lq2d_apply_precond_multi_device",
     "lq2d_autotune",
     "lq2d_batch_create", "lq2d_batch_solve", "lq2d_batch_destroy", "lq2d_get_solution_device",
     "lq2d_set_option",
@@ -87,6 +88,7 @@ def load() -> ctypes.CDLL:
         "lq2d_solve_nbjm_device": (i, [_vp, d, i, i, _vp, _vp, _vp, _ip, _dp, _vp]),
         "lq2d_apply_delta_device": (i, [_vp, _vp, _vp, _vp]),
         "lq2d_apply_precond_device": (i, [_vp, i, i, _vp, _vp, _vp]),
+        "lq2d_apply_precond_multi_device": (i, [_vp, i, i, i, _vp, _vp, _vp]),
         "lq2d_autotune": (i, [_vp, i, i, i, _ip, _dp, _vp]),
         "lq2d_apply_delta_static": (i, [i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lq2d_batch_create": (i, [pp, i, _vp]),
@@ -245,6 +247,12 @@ class Problem:
 
     def apply_precond_device(self, S, L, d_r, d_q, stream=None):
         _check(load().lq2d_apply_precond_device(self._h, S, L, _addr(d_r), _addr(d_q), _stream(stream)))
+
+    def apply_precond_multi_device(self, nrhs, S, L, d_r, d_q, stream=None):
+        """q_r = D_S r_r for nrhs <= 32 right-hand sides [nrhs][T+1][K*N][n]
+        (tensor-core path, n = 4)."""
+        _check(load().lq2d_apply_precond_multi_device(self._h, nrhs, S, L, _addr(d_r), _addr(d_q),
+                                                      _stream(stream)))
 
     def autotune(self, S=2, L=2, reps=5, stream=None):
         """Times the sweep tile widths for this shape and precision mode and
