@@ -209,6 +209,36 @@ int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const v
 int lq2d_apply_precond_multi_device(lq2d_problem *h, int nrhs, int outer_S, int inner_L, const void *d_r,
                                     void *d_q, void *stream);
 
+/* Solves the problem for up to 32 initial states at once (config: many x0
+ * of one instance): Algorithm 1 runs for each right-hand side r_delta(x0_r)
+ * side by side, sharing every product with Delta and every preconditioner
+ * sweep, with the tensor-core preconditioner of
+ * lq2d_apply_precond_multi_device.  Precision as in precision mode 2: r,
+ * delta and d are FP64, the product Delta d is FP32 with the true residual
+ * replacing the recurrence one after each drop of 1e4 (per right-hand
+ * side), beta is the flexible ratio; a right-hand side that meets the
+ * tolerance stops moving while the others go on.  At exit the true
+ * residual of every right-hand side is checked; one that fails restarts
+ * from its iterate (at most LQ2D_OPT_MAX_RESTARTS times).  The stop test is
+ * the relative 2-norm, ||r_delta - Delta delta||_2 <= tol ||r_delta||_2,
+ * whatever LQ2D_OPT_STOP_MODE says.  Boundary terms set by lq2d_set_affine
+ * apply to every right-hand side.
+ *   nrhs       1..32
+ *   d_x0s      device [nrhs][K*N][n], the initial states gamma_r
+ *   d_x, d_u, d_costate  device outputs [nrhs][T+1][K*N][n], [nrhs][T][K*N][m],
+ *              [nrhs][T+1][K*N][n]; any may be NULL
+ *   iterations, rel_residuals  host outputs [nrhs] (may be NULL): PCG steps
+ *              and final true relative residual of each right-hand side
+ * Needs n = 4 (LQ2D_EINVAL otherwise).  Uses the handle's solution
+ * buffers as scratch: lq2d_get_solution_device afterwards returns the last
+ * right-hand side's solution.  LQ2D_ENOCONV when max_iter is reached before
+ * every right-hand side converged (outputs still written), LQ2D_EBREAKDOWN,
+ * LQ2D_ETIMEOUT as for lq2d_solve.  Returns after the work on `stream` is
+ * complete. */
+int lq2d_solve_multi_device(lq2d_problem *h, int nrhs, const void *d_x0s, double tol, int outer_S, int inner_L,
+                            int max_iter, void *d_x, void *d_u, void *d_costate, int *iterations,
+                            double *rel_residuals, void *stream);
+
 /* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS) for this problem's shape
  * and the handle's current precision mode by timing: runs D_S (S outer x L
  * inner sweeps, Algorithm 2) once as warm-up and then `reps` times with each

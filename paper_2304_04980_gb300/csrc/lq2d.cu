@@ -101,6 +101,14 @@ struct lq2d_problem {
   mrhs::Buffers mb{};
   float *m_src = nullptr, *m_thA = nullptr, *m_thB = nullptr, *m_rth = nullptr;
   bool mrhs_built = false;
+  // multi-right-hand-side PCG (allocated on its first solve)
+  mrhs::SolveVecs mv{};
+  mrhs::State* mstate = nullptr;
+  mrhs::State* h_mstate = nullptr;  // pinned mirror
+  double* m_partials = nullptr;
+  cudaGraph_t m_graph = nullptr;
+  cudaGraphExec_t m_exec = nullptr;
+  int m_graph_S = 0, m_graph_L = 0;
 };
 
 // Many problems solved by one graph launch: one independent chain per
@@ -145,6 +153,12 @@ void free_all(lq2d_problem* h) {
   if (h->h_st) cudaFreeHost(h->h_st);
   if (h->h_kkt) cudaFreeHost(h->h_kkt);
   if (h->h_done) cudaFreeHost(h->h_done);
+  if (h->h_mstate) cudaFreeHost(h->h_mstate);
+  if (h->m_exec) cudaGraphExecDestroy(h->m_exec);
+  if (h->m_graph) cudaGraphDestroy(h->m_graph);
+  h->h_mstate = nullptr;
+  h->m_exec = nullptr;
+  h->m_graph = nullptr;
   if (h->priv) cudaStreamDestroy(h->priv);
   h->h_st = nullptr;
   h->h_kkt = nullptr;
@@ -973,6 +987,49 @@ int batch_build(lq2d_batch* b, double tol, int S, int L, int max_iter) {
   return LQ2D_OK;
 }
 
+// FP32 copies of the preconditioner's operands and of the Delta product's
+// blocks (precision modes 1 and 2, and the multi-right-hand-side solve),
+// allocated on first use and refreshed at every setup.
+int ensure_f32(lq2d_problem* h) {
+  if (h->f32_buf) return LQ2D_OK;
+  {
+    long long c[kF32Arrays];
+    prec_counts(h, c);
+    long long total = 0;
+    for (int a = 0; a < kF32Arrays; ++a) total += c[a];
+    double* buf = nullptr;
+    int rc = dev_alloc(h, &buf, (size_t)(total + 1) / 2 + 64);
+    if (rc) return rc;
+    h->f32_buf = reinterpret_cast<float*>(buf);
+    float* p = h->f32_buf;
+    h->pd32.fac = p;
+    p += c[0];
+    h->pd32.Om = p;
+    p += c[1];
+    h->pd32.AQ = p;
+    p += c[2];
+    h->pd32.QAt = p;
+    p += c[3];
+    h->pd32.Qm = p;
+    p += c[4];
+    h->op32.Aself = p;
+    p += c[5];
+    h->op32.Anb = p;
+    p += c[6];
+    h->op32.Qi = p;
+    p += c[7];
+    h->op32.QTi = p;
+    p += c[8];
+    h->op32.Sb = p;
+    h->pd32.fac_rec = h->nd.fac_rec;
+    h->pd32.fac_vc = h->nd.fac_vc;
+    convert_prec_f32(h, nullptr);
+    LQ_CUDA(cudaStreamSynchronize(nullptr));
+    LQ_CUDA(cudaGetLastError());
+  }
+  return LQ2D_OK;
+}
+
 // Float buffer of `count` elements from the handle's allocations.
 int alloc_floats(lq2d_problem* h, float** p, size_t count) {
   double* d = nullptr;
@@ -1008,27 +1065,197 @@ int ensure_mrhs(lq2d_problem* h, cudaStream_t s) {
 
 // q = D_S r for the 32 right-hand sides of m_src (Algorithm 2, S x L sweeps
 // from zero starts); returns the buffer holding q.
-const float* enqueue_precond_multi(lq2d_problem* h, int S, int L, cudaStream_t s) {
+const float* enqueue_precond_multi(lq2d_problem* h, int S, int L, const float* src0, const SolverState* st,
+                                   cudaStream_t s) {
   float* bufs[2] = {h->m_thA, h->m_thB};
   int out_i = 0;
   const float* prev = nullptr;
   for (int so = 0; so < S; ++so) {
     for (int l = 0; l < L; ++l) {
       int variant;
-      const float* src = h->m_src;
+      const float* src = src0;
       if (l == 0 && so == 0) variant = 0;
       else if (l == 0) variant = 2;
       else {
         variant = 1;
         if (so > 0) src = h->m_rth;
       }
-      mrhs::launch_sweep(variant, h->g, h->mb, src, prev, bufs[out_i], h->m_rth, s);
+      mrhs::launch_sweep(variant, h->g, h->mb, src, prev, bufs[out_i], h->m_rth, st, s);
       h->launches += 1;
       prev = bufs[out_i];
       out_i ^= 1;
     }
   }
   return prev;
+}
+
+// Buffers of the multi-right-hand-side PCG: allocated on its first solve.
+int ensure_mrhs_solve(lq2d_problem* h) {
+  int rc = ensure_f32(h);
+  if (rc != LQ2D_OK) return rc;
+  if (h->mstate) return LQ2D_OK;
+  const Grid& g = h->g;
+  const size_t vec = (size_t)mrhs::vec_floats(g);
+  mrhs::SolveVecs& v = h->mv;
+  if ((rc = dev_alloc(h, &v.rhs, vec)) != LQ2D_OK) return rc;
+  if ((rc = dev_alloc(h, &v.r, vec)) != LQ2D_OK) return rc;
+  if ((rc = dev_alloc(h, &v.delta, vec)) != LQ2D_OK) return rc;
+  if ((rc = dev_alloc(h, &v.d, vec)) != LQ2D_OK) return rc;
+  if ((rc = dev_alloc(h, &v.y64, vec)) != LQ2D_OK) return rc;
+  if ((rc = dev_alloc(h, &v.z64, vec)) != LQ2D_OK) return rc;
+  if ((rc = alloc_floats(h, &v.d32, vec)) != LQ2D_OK) return rc;
+  if ((rc = alloc_floats(h, &v.z32, vec)) != LQ2D_OK) return rc;
+  if ((rc = alloc_floats(h, &v.y32, vec)) != LQ2D_OK) return rc;
+  v.r32 = h->m_src;  // the preconditioner's source
+  if ((rc = dev_alloc(h, &h->m_partials, (size_t)mrhs::solve_blocks(g) * 2 * mrhs::kRhs + 64)) != LQ2D_OK)
+    return rc;
+  double* st = nullptr;
+  if ((rc = dev_alloc(h, &st, (sizeof(mrhs::State) + 7) / 8)) != LQ2D_OK) return rc;
+  LQ_CUDA(cudaMemset(st, 0, sizeof(mrhs::State)));
+  LQ_CUDA(cudaMallocHost(&h->h_mstate, sizeof(mrhs::State)));
+  h->mstate = reinterpret_cast<mrhs::State*>(st);
+  return LQ2D_OK;
+}
+
+// The preconditioner's output buffer of the multi-right-hand-side loop
+// (S*L sweeps alternate between two buffers; S*L is even).
+float* multi_q(lq2d_problem* h) { return h->m_thB; }
+
+// One step of the multi-right-hand-side PCG: the product and alpha, the
+// update and tests, the preconditioner, mu and beta, then the residual
+// replacements that are due.
+void enqueue_multi_step(lq2d_problem* h, int S, int L, cudaStream_t s) {
+  const Grid& g = h->g;
+  mrhs::launch_delta_loop(g, h->op32, multi_q(h), h->mv, h->m_partials, h->mstate, h->st, s);
+  mrhs::launch_update(g, h->mv, h->m_partials, h->mstate, h->st, s);
+  enqueue_precond_multi(h, S, L, h->mv.r32, h->st, s);
+  mrhs::launch_mu(g, multi_q(h), h->mv, h->m_partials, h->mstate, h->st, s);
+  mrhs::launch_replace(g, h->op64, h->mv, h->m_partials, h->mstate, h->st, false, s);
+}
+
+constexpr int kMultiStepKernels = 7;  // besides the S*L sweeps
+
+int get_multi_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
+  if (h->m_exec && h->m_graph_S == S && h->m_graph_L == L) {
+    *exec = h->m_exec;
+    return LQ2D_OK;
+  }
+  if (h->m_exec) cudaGraphExecDestroy(h->m_exec);
+  if (h->m_graph) cudaGraphDestroy(h->m_graph);
+  h->m_exec = nullptr;
+  h->m_graph = nullptr;
+  cudaGraph_t graph;
+  LQ_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle hc;
+  LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, graph, 1u, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_storage, 0, sizeof(cp_storage));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  LQ_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  LQ_CUDA(cudaStreamBeginCaptureToGraph(h->priv, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const long long before = h->launches;
+  enqueue_multi_step(h, S, L, h->priv);
+  h->launches = before;
+  launch_loop_ctrl(h->st, hc, h->priv);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(h->priv, &captured);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(LQ2D_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaGraphInstantiate(&h->m_exec, graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(LQ2D_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+  }
+  h->m_graph = graph;
+  h->m_graph_S = S;
+  h->m_graph_L = L;
+  *exec = h->m_exec;
+  return LQ2D_OK;
+}
+
+// The whole multi-right-hand-side solve on device buffers, ordered on s.
+int solve_multi_impl(lq2d_problem* h, int nrhs, const double* d_x0s, double tol, int S, int L, int max_iter,
+                     double* d_x, double* d_u, double* d_costate, int* iterations, double* rel_res,
+                     cudaStream_t s) {
+  int rc = ensure_mrhs(h, s);
+  if (rc == LQ2D_OK) rc = ensure_mrhs_solve(h);
+  if (rc != LQ2D_OK) return rc;
+  const Grid& g = h->g;
+  const double rho2 = kPhaseRho * kPhaseRho;
+  mrhs::launch_init(g, nrhs, d_x0s, h->rhs, g.Ps, h->mv, h->m_partials, h->mstate, h->st, tol, rho2, max_iter, s);
+  h->launches += 1;
+  int restarts = 0;
+  int status = LQ2D_OK;
+  long long bodies = 0;
+  for (;;) {
+    // first direction: q = P^-1 r, mu (beta = 0)
+    enqueue_precond_multi(h, S, L, h->mv.r32, h->st, s);
+    mrhs::launch_mu(g, multi_q(h), h->mv, h->m_partials, h->mstate, h->st, s);
+    LQ_CUDA(cudaMemsetAsync(h->mv.d, 0, (size_t)mrhs::vec_floats(g) * sizeof(double), s));
+    LQ_CUDA(cudaMemsetAsync(h->mv.d32, 0, (size_t)mrhs::vec_floats(g) * sizeof(float), s));
+    h->launches += S * L + 1;
+    cudaGraphExec_t exec;
+    rc = get_multi_graph(h, S, L, &exec);
+    if (rc != LQ2D_OK) return rc;
+    LQ_CUDA(cudaGraphLaunch(exec, s));
+    // the true residual of every right-hand side decides convergence
+    mrhs::launch_replace(g, h->op64, h->mv, h->m_partials, h->mstate, h->st, true, s);
+    h->launches += 3;
+    LQ_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    LQ_CUDA(cudaMemcpyAsync(h->h_mstate, h->mstate, sizeof(mrhs::State), cudaMemcpyDeviceToHost, s));
+    LQ_CUDA(cudaStreamSynchronize(s));
+    LQ_CUDA(cudaGetLastError());
+    const SolverState& hs = *h->h_st;
+    const mrhs::State& ms = *h->h_mstate;
+    h->launches += (long long)(hs.body_count - bodies) * (kMultiStepKernels + S * L + 1);
+    bodies = hs.body_count;
+    if (ms.breakdown || hs.done == kBreakdown) { status = LQ2D_EBREAKDOWN; break; }
+    if (hs.done == kConverged) break;
+    if (hs.body_count >= hs.body_cap) { status = LQ2D_ETIMEOUT; break; }
+    if (hs.iter >= max_iter || restarts >= h->max_restarts) { status = LQ2D_ENOCONV; break; }
+    // a recurrence residual passed while the true one did not: restart the
+    // right-hand sides concerned from their current iterate
+    ++restarts;
+    const int zero = 0;
+    LQ_CUDA(cudaMemcpyAsync(&h->mstate->have_mu, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    LQ_CUDA(cudaStreamSynchronize(s));
+  }
+  // outputs: recovery (Section II-B) per right-hand side through the
+  // single-right-hand-side buffers
+  const long long nx = (long long)(g.T + 1) * g.NN * g.n, nu = (long long)g.T * g.NN * g.m;
+  for (int r = 0; r < nrhs; ++r) {
+    mrhs::launch_gather(g, h->mv.delta, r, h->delta, s);
+    h->kt->delta_z(g, h->op64, h->delta, nullptr, h->z, nullptr, 0, s);
+    launch_recover_u(g, h->nd, h->delta, h->u, s);
+    if (d_x) launch_to_api(h->z, d_x + r * nx, g.NN, g.T + 1, g.n, g.Ps, s);
+    if (d_u) launch_to_api(h->u, d_u + r * nu, g.NN, g.T, g.m, g.Pus, s);
+    if (d_costate) launch_to_api(h->delta, d_costate + r * nx, g.NN, g.T + 1, g.n, g.Ps, s);
+    h->launches += 3 + (d_x != nullptr) + (d_u != nullptr) + (d_costate != nullptr);
+  }
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(cudaGetLastError());
+  const mrhs::State& ms = *h->h_mstate;
+  int iters_max = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    if (iterations) iterations[r] = ms.iters[r];
+    if (rel_res) rel_res[r] = ms.bnorm2[r] > 0 ? std::sqrt(ms.rnorm2[r] / ms.bnorm2[r]) : std::sqrt(ms.rnorm2[r]);
+    iters_max = std::max(iters_max, ms.iters[r]);
+  }
+  h->stats.iterations = iters_max;
+  h->stats.restarts = restarts;
+  h->stats.status = status;
+  if (status == LQ2D_ENOCONV) return fail(status, "max_iter reached before every right-hand side met the tolerance");
+  if (status == LQ2D_EBREAKDOWN) return fail(status, "breakdown: y'd <= 0 or a non-finite scalar");
+  if (status == LQ2D_ETIMEOUT) return fail(status, "device loop cap reached");
+  return LQ2D_OK;
 }
 
 }  // namespace
@@ -1201,12 +1428,27 @@ int lq2d_apply_precond_multi_device(lq2d_problem* h, int nrhs, int S, int L, con
   int rc = ensure_mrhs(h, s);
   if (rc != LQ2D_OK) return rc;
   mrhs::launch_from_api(h->g, nrhs, static_cast<const double*>(d_r), h->m_src, s);
-  const float* q = enqueue_precond_multi(h, S, L, s);
+  const float* q = enqueue_precond_multi(h, S, L, h->m_src, nullptr, s);
   mrhs::launch_to_api(h->g, nrhs, q, static_cast<double*>(d_q), s);
   h->launches += 2;
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
   return LQ2D_OK;
+}
+
+int lq2d_solve_multi_device(lq2d_problem* h, int nrhs, const void* d_x0s, double tol, int S, int L, int max_iter,
+                            void* d_x, void* d_u, void* d_costate, int* iterations, double* rel_residuals,
+                            void* stream) {
+  if (!h || !d_x0s) return fail(LQ2D_EINVAL, "null argument");
+  if (h->g.n != mrhs::kN) return fail(LQ2D_EINVAL, "the multi-right-hand-side path needs n = 4");
+  if (nrhs < 1 || nrhs > mrhs::kRhs) return fail(LQ2D_EINVAL, "nrhs must be in 1..32");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(LQ2D_EINVAL, "tol must be positive");
+  if (S < 1) return fail(LQ2D_EINVAL, "outer_S must be >= 1");
+  if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2");
+  if (max_iter < 0) return fail(LQ2D_EINVAL, "max_iter must be >= 0");
+  return solve_multi_impl(h, nrhs, static_cast<const double*>(d_x0s), tol, S, L, max_iter, static_cast<double*>(d_x),
+                          static_cast<double*>(d_u), static_cast<double*>(d_costate), iterations, rel_residuals,
+                          static_cast<cudaStream_t>(stream));
 }
 
 int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double* ms, void* stream) {
@@ -1418,40 +1660,9 @@ int lq2d_set_precision(lq2d_problem* h, int mode) {
     h->d32 = reinterpret_cast<float*>(buf);
     LQ_CUDA(cudaMemset(h->d32, 0, (size_t)h->g.Ps * h->g.n * sizeof(float)));
   }
-  if (mode >= 1 && !h->f32_buf) {
-    long long c[kF32Arrays];
-    prec_counts(h, c);
-    long long total = 0;
-    for (int a = 0; a < kF32Arrays; ++a) total += c[a];
-    double* buf = nullptr;
-    int rc = dev_alloc(h, &buf, (size_t)(total + 1) / 2 + 64);
-    if (rc) return rc;
-    h->f32_buf = reinterpret_cast<float*>(buf);
-    float* p = h->f32_buf;
-    h->pd32.fac = p;
-    p += c[0];
-    h->pd32.Om = p;
-    p += c[1];
-    h->pd32.AQ = p;
-    p += c[2];
-    h->pd32.QAt = p;
-    p += c[3];
-    h->pd32.Qm = p;
-    p += c[4];
-    h->op32.Aself = p;
-    p += c[5];
-    h->op32.Anb = p;
-    p += c[6];
-    h->op32.Qi = p;
-    p += c[7];
-    h->op32.QTi = p;
-    p += c[8];
-    h->op32.Sb = p;
-    h->pd32.fac_rec = h->nd.fac_rec;
-    h->pd32.fac_vc = h->nd.fac_vc;
-    convert_prec_f32(h, nullptr);
-    LQ_CUDA(cudaStreamSynchronize(nullptr));
-    LQ_CUDA(cudaGetLastError());
+  if (mode >= 1) {
+    const int rc = ensure_f32(h);
+    if (rc != LQ2D_OK) return rc;
   }
   h->precision = mode;
   return LQ2D_OK;

@@ -90,30 +90,30 @@ __device__ __forceinline__ void d_load(const float* P, int tile, int g, int q, f
   d[3] = P[(2 * q + 1) * kPs + m + 8];
 }
 
-// Writes a D fragment of tile `tile` (rows = pair-row unknowns a = jj*4 + k,
-// columns = right-hand sides) to a vector at pair-row i, time t.
-__device__ __forceinline__ void d_to_global(float* vec, const Grid& g, long long plane, int i, int j0, bool two,
-                                            int t, int tile, int gq, int q, const float (&d)[4]) {
-  const int Tp = g.T + 1;
+// Writes an 8 x 32 panel P[a][rhs] (pair-row unknown a = jj*4 + k) to a
+// vector as 16-byte chunks: lane (k = lane / 8, chunk = lane % 8) writes
+// row a = 4 jj + k for jj = 0, 1.  pt0 is the (node, time) offset of the
+// pair's first node, times 32; the second node follows at + (T+1)*32.
+__device__ __forceinline__ void panel_to_global(float* vec, const float* P, long long plane, long long pt0,
+                                                long long node_step, bool two, int lane) {
+  const int k = lane >> 3, ch = lane & 7;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int row = 2 * q + (e & 1);
-    const int m = gq + 8 * (e >> 1) + 16 * tile;
-    const int jj = row >> 2, k = row & 3;
+  for (int jj = 0; jj < 2; ++jj) {
     if (jj == 1 && !two) continue;
-    vec[k * plane + ((long long)(i * g.N + j0 + jj) * Tp + t) * kRhs + m] = d[e];
+    const float4 val = *reinterpret_cast<const float4*>(P + (4 * jj + k) * kPs + ch * 4);
+    *reinterpret_cast<float4*>(vec + k * plane + pt0 + jj * node_step + ch * 4) = val;
   }
 }
 
 template <int NW>
 struct Layout {
   // offsets in floats of the dynamic shared memory
-  static constexpr int rec = 0;                               // [kNb][3][kRec]
-  static constexpr int w = rec + kNb * 3 * kRec;              // [kNb][NW][kW]
-  static constexpr int src = w + kNb * NW * kW;               // [kNb][kWpc][8][kPs]
-  static constexpr int halo = src + kNb * kWpc * 8 * kPs;     // [kNb][kWpc][NW][32][kPs]
+  static constexpr int rec = 0;                                   // [kNb][3][kRec]
+  static constexpr int w = rec + kNb * 3 * kRec;                  // [kNb][NW][kW]
+  static constexpr int src = w + kNb * NW * kW;                   // [kNb][kWpc][8][kPs]
+  static constexpr int halo = src + kNb * kWpc * 8 * kPs;         // [kNb][kWpc][NW][32][kPs]
   static constexpr int ring = halo + kNb * kWpc * NW * 32 * kPs;  // [kWpc][3][8][kPs]
-  static constexpr int xch = ring + kWpc * 3 * 8 * kPs;       // [kWpc][8][kPs]
+  static constexpr int xch = ring + kWpc * 3 * 8 * kPs;           // [kWpc][8][kPs]
   static constexpr int total = xch + kWpc * 8 * kPs;
 };
 
@@ -122,12 +122,18 @@ struct Layout {
 // pair-rows together, and for pair-row i+1 the CTA stages with cp.async
 // (two buffers) the record (all three classes), the coupling matrices, and
 // per warp its 8 x 32 panel of tau's source (forward) or of y_i (backward)
-// and its neighbours' 32 x 32 panels (coupling term).
+// and its neighbours' 32 x 32 panels (coupling term).  Every staged row is
+// 32 right-hand sides = 8 chunks of 16 bytes, and a lane always copies the
+// same chunk of the same component, so its global offsets are fixed up to a
+// shift of one grid row (N (T+1) 32 floats) per pair-row and are computed
+// once.
 template <int VAR>
 __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers bf, const float* __restrict__ src,
                                                                const float* __restrict__ th_in,
                                                                float* __restrict__ th_out,
-                                                               float* __restrict__ rth_out) {
+                                                               float* __restrict__ rth_out,
+                                                               const SolverState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
   constexpr int NW = VAR == 0 ? 0 : (VAR == 1 ? 1 : 2);
   using Ly = Layout<NW>;
   extern __shared__ __align__(16) float smf[];
@@ -143,11 +149,42 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
   const bool active = t <= g.T;
   const int cls = t == 0 ? 2 : (t == g.T ? 1 : 0);
   const long long plane = (long long)g.NN * Tp * kRhs;
-  const bool xi = VAR == 2;
+  const long long row_step = (long long)g.N * Tp * kRhs;  // one grid row
+  const long long node_step = (long long)Tp * kRhs;        // one node
+  // this lane's component and chunk in every staged or written row
+  const int lk = lane >> 3, lch = lane & 7;
+  const long long own0 = (long long)lk * plane + ((long long)j0 * Tp + t) * kRhs + lch * 4;  // pair-row 0, jj = 0
+
+  // halo rows (h, c = lk) of the eight staged neighbours: node offset from
+  // the pair's first node (j0) of pair-row 0, and which of them exist
+  long long hoff[8];
+  unsigned col_ok = 0u, above = 0u, below = 0u;
+  if (NW > 0) {
+    const unsigned long long packed = VAR == 2 ? hot::kXiPacked : hot::kOmPacked;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const unsigned code = (unsigned)((packed >> (5 * h)) & 31ull);
+      const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
+      if (jn >= 0 && jn < g.N) col_ok |= 1u << h;
+      if (di < 0) above |= 1u << h;
+      if (di > 0) below |= 1u << h;
+      hoff[h] = (long long)lk * plane + ((long long)(di * g.N + jn) * Tp) * kRhs + lch * 4;
+    }
+  }
+  // time slices of the halo panels and whether they exist (warp-uniform)
+  int tn[2] = {t, t};
+  bool tok[2] = {false, false};
+  if (VAR == 1) tok[0] = active && t >= 1;
+  if (VAR == 2) {
+    tn[0] = t - 1;
+    tn[1] = t + 1;
+    tok[0] = active && t >= 1;
+    tok[1] = active && t < g.T;
+  }
 
   // ---- staging of pair-row i into buffer b (fwd: forward pass)
   auto stage = [&](int i, int b, bool fwd) {
-    // records of the three classes
+    // records of the three classes, then the coupling matrices
     for (int e = tid; e < 3 * kRec / 4; e += kWpc * 32) {
       const int c = e / (kRec / 4), off = (e % (kRec / 4)) * 4;
       cp16z(smf + Ly::rec + (b * 3 + c) * kRec + off, bf.rec + (((size_t)v * 3 + c) * g.K + i) * kRec + off, true);
@@ -161,26 +198,25 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
     }
     // this warp's 8 x 32 panel: tau's source (forward) or y_i (backward)
     const float* pv = fwd ? src : th_out;
-    for (int e = lane; e < 64; e += 32) {
-      const int a = e >> 3, ch = e & 7;
-      const int jj = a >> 2, k = a & 3;
+    const long long rb = (long long)i * row_step;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
       const bool ok = active && (jj == 0 || two);
-      const long long go = ok ? k * plane + ((long long)(i * g.N + j0 + jj) * Tp + t) * kRhs + ch * 4 : 0;
-      cp16z(smf + Ly::src + ((b * kWpc + w) * 8 + a) * kPs + ch * 4, pv + go, ok);
+      cp16z(smf + Ly::src + ((b * kWpc + w) * 8 + 4 * jj + lk) * kPs + lch * 4,
+            pv + (ok ? own0 + rb + jj * node_step : 0), ok);
     }
     if (fwd && NW > 0) {
-      // neighbour panels: rows (h, c) of the eight staged nodes
+      unsigned rows = col_ok;
+      if (i < 1) rows &= ~above;
+      if (i + 1 >= g.K) rows &= ~below;
 #pragma unroll
       for (int qq = 0; qq < NW; ++qq) {
-        const int tn = VAR == 1 ? t : (qq == 0 ? t - 1 : t + 1);
-        const bool t_ok = active && tn >= 0 && tn <= g.T && (VAR != 1 || t >= 1);
-        for (int e = lane; e < 256; e += 32) {
-          const int row = e >> 3, ch = e & 7;
-          const int h = row >> 2, c = row & 3;
-          const int node = hot::staged_node(xi, h, i, j0, g.K, g.N);
-          const bool ok = t_ok && node >= 0;
-          const long long go = ok ? c * plane + ((long long)node * Tp + tn) * kRhs + ch * 4 : 0;
-          cp16z(smf + Ly::halo + (((b * kWpc + w) * NW + qq) * 32 + row) * kPs + ch * 4, th_in + go, ok);
+        float* dst = smf + Ly::halo + (((b * kWpc + w) * NW + qq) * 32 + lk) * kPs + lch * 4;
+        const long long tb = rb + (long long)tn[qq] * kRhs;
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const bool ok = tok[qq] && ((rows >> h) & 1u);
+          cp16z(dst + 4 * h * kPs, th_in + (ok ? hoff[h] + tb : 0), ok);
         }
       }
     }
@@ -199,6 +235,7 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
     if (i + 1 < g.K) stage(i + 1, b ^ 1, true);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     if (!active) continue;
+    const long long pt0 = ((long long)(i * g.N + j0) * Tp + t) * kRhs;
     const float* P = smf + Ly::src + ((b * kWpc + w) * 8) * kPs;
     float d[2][4];
     d_load(P, 0, gq, q, d[0]);
@@ -206,68 +243,62 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
     if (NW > 0) {
 #pragma unroll
       for (int qq = 0; qq < NW; ++qq) {
-        const bool use = VAR == 1 ? t >= 1 : (qq == 0 ? t >= 1 : t < g.T);
-        if (!use) continue;
+        if (!tok[qq]) continue;
         const float* H = smf + Ly::halo + ((b * kWpc + w) * NW + qq) * 32 * kPs;
         const float* W = smf + Ly::w + (b * NW + qq) * kW;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-          const unsigned b0 = __float_as_uint(W[s * 64 + 2 * lane]);
-          const unsigned b1 = __float_as_uint(W[s * 64 + 2 * lane + 1]);
+          const float2 bw = *reinterpret_cast<const float2*>(W + s * 64 + 2 * lane);
 #pragma unroll
           for (int tile = 0; tile < 2; ++tile) {
             unsigned a[4];
             a_frag(H, 8 * s, tile, gq, q, a);
-            mma_tf32(d[tile], a, b0, b1);
+            mma_tf32(d[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
           }
         }
-      }
-      if (VAR == 2) {
-        d_to_global(rth_out, g, plane, i, j0, two, t, 0, gq, q, d[0]);
-        d_to_global(rth_out, g, plane, i, j0, two, t, 1, gq, q, d[1]);
       }
     }
     // tau to the exchange panel, then y = L0^-1 tau - M2 y_{i-2} - M1 y_{i-1}
     d_store(xch, 0, gq, q, d[0]);
     d_store(xch, 1, gq, q, d[1]);
     __syncwarp();
+    if (VAR == 2) panel_to_global(rth_out, xch, plane, pt0, node_step, two, lane);
     const float* R = smf + Ly::rec + (b * 3 + cls) * kRec;
     float y[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     {
-      const unsigned b0 = __float_as_uint(R[5 * 64 + 2 * lane]), b1 = __float_as_uint(R[5 * 64 + 2 * lane + 1]);
+      const float2 bw = *reinterpret_cast<const float2*>(R + 5 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
         a_frag(xch, 0, tile, gq, q, a);
-        mma_tf32(y[tile], a, b0, b1);
+        mma_tf32(y[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
     }
     if (i >= 2 && cls != 2) {
       const float* Y2 = ring + ((i - 2) % 3) * 8 * kPs;
-      const unsigned b0 = __float_as_uint(R[3 * 64 + 2 * lane]), b1 = __float_as_uint(R[3 * 64 + 2 * lane + 1]);
+      const float2 bw = *reinterpret_cast<const float2*>(R + 3 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
         a_frag(Y2, 0, tile, gq, q, a);
-        mma_tf32(y[tile], a, b0, b1);
+        mma_tf32(y[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
     }
     if (i >= 1 && cls != 2) {
       const float* Y1 = ring + ((i - 1) % 3) * 8 * kPs;
-      const unsigned b0 = __float_as_uint(R[4 * 64 + 2 * lane]), b1 = __float_as_uint(R[4 * 64 + 2 * lane + 1]);
+      const float2 bw = *reinterpret_cast<const float2*>(R + 4 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
         a_frag(Y1, 0, tile, gq, q, a);
-        mma_tf32(y[tile], a, b0, b1);
+        mma_tf32(y[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
     }
     float* Y0 = ring + (i % 3) * 8 * kPs;
     d_store(Y0, 0, gq, q, y[0]);
     d_store(Y0, 1, gq, q, y[1]);
-    d_to_global(th_out, g, plane, i, j0, two, t, 0, gq, q, y[0]);
-    d_to_global(th_out, g, plane, i, j0, two, t, 1, gq, q, y[1]);
     __syncwarp();
+    panel_to_global(th_out, Y0, plane, pt0, node_step, two, lane);
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
@@ -282,44 +313,44 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
     if (i >= 1) stage(i - 1, b ^ 1, false);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     if (!active || cls == 2) continue;
+    const long long pt0 = ((long long)(i * g.N + j0) * Tp + t) * kRhs;
     const float* P = smf + Ly::src + ((b * kWpc + w) * 8) * kPs;
     const float* R = smf + Ly::rec + (b * 3 + cls) * kRec;
     float x[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     {
-      const unsigned b0 = __float_as_uint(R[2 * 64 + 2 * lane]), b1 = __float_as_uint(R[2 * 64 + 2 * lane + 1]);
+      const float2 bw = *reinterpret_cast<const float2*>(R + 2 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
         a_frag(P, 0, tile, gq, q, a);
-        mma_tf32(x[tile], a, b0, b1);
+        mma_tf32(x[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
     }
     if (i + 2 < g.K) {
       const float* X2 = ring + ((i + 2) % 3) * 8 * kPs;
-      const unsigned b0 = __float_as_uint(R[0 * 64 + 2 * lane]), b1 = __float_as_uint(R[0 * 64 + 2 * lane + 1]);
+      const float2 bw = *reinterpret_cast<const float2*>(R + 0 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
         a_frag(X2, 0, tile, gq, q, a);
-        mma_tf32(x[tile], a, b0, b1);
+        mma_tf32(x[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
     }
     if (i + 1 < g.K) {
       const float* X1 = ring + ((i + 1) % 3) * 8 * kPs;
-      const unsigned b0 = __float_as_uint(R[1 * 64 + 2 * lane]), b1 = __float_as_uint(R[1 * 64 + 2 * lane + 1]);
+      const float2 bw = *reinterpret_cast<const float2*>(R + 1 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
         a_frag(X1, 0, tile, gq, q, a);
-        mma_tf32(x[tile], a, b0, b1);
+        mma_tf32(x[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
     }
     float* X0 = ring + (i % 3) * 8 * kPs;
     d_store(X0, 0, gq, q, x[0]);
     d_store(X0, 1, gq, q, x[1]);
-    d_to_global(th_out, g, plane, i, j0, two, t, 0, gq, q, x[0]);
-    d_to_global(th_out, g, plane, i, j0, two, t, 1, gq, q, x[1]);
     __syncwarp();
+    panel_to_global(th_out, X0, plane, pt0, node_step, two, lane);
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
@@ -389,30 +420,48 @@ __global__ void mrhs_coupling_kernel(Grid g, NodeData nd, float* wom, float* wxa
   }
 }
 
-// api [nrhs][T+1][NN][n] <-> vector [n][NN][T+1][32], one thread per vector element.
-__global__ void from_api_kernel(Grid g, int nrhs, const double* __restrict__ api, float* __restrict__ vec) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// api [nrhs][T+1][NN][n] <-> vector [n][NN][T+1][32] by 32 x 32 tiles
+// through shared memory: for one time t, the api slice is a matrix
+// [rhs][c] with c = node*n + k, and the vector holds its transpose in rows
+// of 32 right-hand sides.  A CTA of 32 x 8 threads moves the tile of
+// columns c0 .. c0+31 at time t = blockIdx.y, reading and writing 32
+// consecutive elements per warp access on both sides.
+template <typename FT, typename TT, bool TO_VEC>
+__global__ void transpose_kernel(Grid g, int nrhs, const FT* __restrict__ in, TT* __restrict__ out) {
+  __shared__ float tile[32][33];
   const int Tp = g.T + 1;
-  const long long total = (long long)kN * g.NN * Tp * kRhs;
-  if (e >= total) return;
-  const int r = (int)(e % kRhs);
-  const long long pt = (e / kRhs) % ((long long)g.NN * Tp);
-  const int k = (int)(e / ((long long)kRhs * g.NN * Tp));
-  const int p = (int)(pt / Tp), t = (int)(pt % Tp);
-  vec[e] = r < nrhs ? (float)api[(((long long)r * Tp + t) * g.NN + p) * kN + k] : 0.f;
-}
-
-__global__ void to_api_kernel(Grid g, int nrhs, const float* __restrict__ vec, double* __restrict__ api) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int Tp = g.T + 1;
-  const long long total = (long long)kN * g.NN * Tp * kRhs;
-  if (e >= total) return;
-  const int r = (int)(e % kRhs);
-  if (r >= nrhs) return;
-  const long long pt = (e / kRhs) % ((long long)g.NN * Tp);
-  const int k = (int)(e / ((long long)kRhs * g.NN * Tp));
-  const int p = (int)(pt / Tp), t = (int)(pt % Tp);
-  api[(((long long)r * Tp + t) * g.NN + p) * kN + k] = (double)vec[e];
+  const long long C = (long long)g.NN * kN;
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int t = blockIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long plane = (long long)g.NN * Tp * kRhs;
+  if (TO_VEC) {
+    for (int r = ty; r < 32; r += 8) {
+      const long long c = c0 + tx;
+      float val = 0.f;
+      if (r < nrhs && c < C) val = (float)in[((long long)r * Tp + t) * C + c];
+      tile[r][tx] = val;
+    }
+    __syncthreads();
+    for (int cc = ty; cc < 32; cc += 8) {
+      const long long c = c0 + cc;
+      if (c >= C) continue;
+      const long long p = c / kN, k = c % kN;
+      out[k * plane + (p * Tp + t) * kRhs + tx] = (TT)tile[tx][cc];
+    }
+  } else {
+    for (int cc = ty; cc < 32; cc += 8) {
+      const long long c = c0 + cc;
+      if (c >= C) continue;
+      const long long p = c / kN, k = c % kN;
+      tile[tx][cc] = (float)in[k * plane + (p * Tp + t) * kRhs + tx];
+    }
+    __syncthreads();
+    for (int r = ty; r < nrhs; r += 8) {
+      const long long c = c0 + tx;
+      if (c < C) out[((long long)r * Tp + t) * C + c] = (TT)tile[r][tx];
+    }
+  }
 }
 
 template <int VAR>
@@ -432,22 +481,28 @@ void launch_build(const Grid& g, const NodeData& nd, const Buffers& b, cudaStrea
 }
 
 void launch_from_api(const Grid& g, int nrhs, const double* api, float* vec, cudaStream_t s) {
-  const long long total = vec_floats(g);
-  from_api_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, nrhs, api, vec);
+  const dim3 grid((unsigned)(((long long)g.NN * kN + 31) / 32), (unsigned)(g.T + 1));
+  transpose_kernel<double, float, true><<<grid, dim3(32, 8), 0, s>>>(g, nrhs, api, vec);
 }
 
 void launch_to_api(const Grid& g, int nrhs, const float* vec, double* api, cudaStream_t s) {
-  const long long total = vec_floats(g);
-  to_api_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, nrhs, vec, api);
+  const dim3 grid((unsigned)(((long long)g.NN * kN + 31) / 32), (unsigned)(g.T + 1));
+  transpose_kernel<float, double, false><<<grid, dim3(32, 8), 0, s>>>(g, nrhs, vec, api);
 }
 
 void launch_sweep(int variant, const Grid& g, const Buffers& b, const float* src, const float* theta_in,
-                  float* theta_out, float* rth_out, cudaStream_t s) {
+                  float* theta_out, float* rth_out, const SolverState* st, cudaStream_t s) {
   const unsigned blocks = (unsigned)((long long)g.V * ((g.T + 1 + kWpc - 1) / kWpc));
   switch (variant) {
-    case 0: mrhs_sweep_kernel<0><<<blocks, kWpc * 32, smem_bytes<0>(), s>>>(g, b, src, theta_in, theta_out, rth_out); break;
-    case 1: mrhs_sweep_kernel<1><<<blocks, kWpc * 32, smem_bytes<1>(), s>>>(g, b, src, theta_in, theta_out, rth_out); break;
-    default: mrhs_sweep_kernel<2><<<blocks, kWpc * 32, smem_bytes<2>(), s>>>(g, b, src, theta_in, theta_out, rth_out); break;
+    case 0:
+      mrhs_sweep_kernel<0><<<blocks, kWpc * 32, smem_bytes<0>(), s>>>(g, b, src, theta_in, theta_out, rth_out, st);
+      break;
+    case 1:
+      mrhs_sweep_kernel<1><<<blocks, kWpc * 32, smem_bytes<1>(), s>>>(g, b, src, theta_in, theta_out, rth_out, st);
+      break;
+    default:
+      mrhs_sweep_kernel<2><<<blocks, kWpc * 32, smem_bytes<2>(), s>>>(g, b, src, theta_in, theta_out, rth_out, st);
+      break;
   }
 }
 

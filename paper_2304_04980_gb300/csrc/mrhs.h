@@ -4,7 +4,7 @@
 // operands, FP32 accumulation).  State dimension n = 4 only.
 #pragma once
 
-#include "common.cuh"
+#include "kernels.h"
 
 namespace lq2d {
 namespace mrhs {
@@ -45,8 +45,60 @@ void launch_to_api(const Grid& g, int nrhs, const float* vec, double* api, cudaS
 //   variant 0: tau = src
 //   variant 1: tau = src + Omega~ theta_in
 //   variant 2: tau = src + Xi~ theta_in, also written to rth_out
+// st (may be NULL): the sweep returns at once when st->done is set.
 void launch_sweep(int variant, const Grid& g, const Buffers& b, const float* src, const float* theta_in,
-                  float* theta_out, float* rth_out, cudaStream_t s);
+                  float* theta_out, float* rth_out, const SolverState* st, cudaStream_t s);
+
+// ---- multi-right-hand-side PCG (Algorithm 1 for each right-hand side)
+//
+// Per-right-hand-side scalars of the Krylov loop; the loop's own state
+// (iteration count, stop flag, body counter) is a SolverState.
+struct State {
+  double mu[kRhs], beta[kRhs], alpha[kRhs];
+  double rnorm2[kRhs], bnorm2[kRhs], rref2[kRhs];
+  int conv[kRhs];   // the residual met the tolerance: this right-hand side is frozen
+  int repl[kRhs];   // its residual is due for replacement by the true one
+  int iters[kRhs];  // PCG steps taken by it
+  int nrhs, any_repl, have_mu, breakdown;
+  double tol2, rho2;
+  unsigned int counter;
+  int pad;
+};
+
+// Vectors of the loop, all [n][K*N][T+1][32]: FP64 rhs, r, delta, d and the
+// FP64 product of a replacement; FP32 copies and products.
+struct SolveVecs {
+  double *rhs, *r, *delta, *d, *y64, *z64;
+  float *d32, *z32, *y32, *r32;
+};
+
+// Blocks of the element-wise kernels (grid-stride over (node, t), one warp
+// per (node, t), lane = right-hand side) and their partial-sum slots.
+int solve_blocks(const Grid& g);
+
+// r = r_delta (x0s [nrhs][K*N][n] at t = 0, rhs1 [n][..] of the problem's
+// own right-hand side at t >= 1), delta = d = 0, norms and state.
+void launch_init(const Grid& g, int nrhs, const double* x0s, const double* rhs1, long long rhs1_stride,
+                 const SolveVecs& v, double* partials, State* ms, SolverState* st, double tol, double rho2,
+                 int max_iter, cudaStream_t s);
+// y32 = Delta d_new with d_new = q + beta d (FP32 product, FP64 d), y' d_new
+// and alpha per right-hand side.
+void launch_delta_loop(const Grid& g, const OpData<float>& op, const float* q, const SolveVecs& v,
+                       double* partials, State* ms, SolverState* st, cudaStream_t s);
+// delta += alpha d, r -= alpha y (right-hand sides not yet converged),
+// norms, stop and replacement tests.
+void launch_update(const Grid& g, const SolveVecs& v, double* partials, State* ms, SolverState* st, cudaStream_t s);
+// mu = q' r and beta (flexible ratio) per right-hand side.
+void launch_mu(const Grid& g, const float* q, const SolveVecs& v, double* partials, State* ms, SolverState* st,
+               cudaStream_t s);
+// r = r_delta - Delta delta in FP64 for the right-hand sides due for
+// replacement (force: all of them, then the convergence flags follow the
+// true residual); gated on the state unless forced.
+void launch_replace(const Grid& g, const OpData<double>& op, const SolveVecs& v, double* partials, State* ms,
+                    SolverState* st, bool force, cudaStream_t s);
+// Right-hand side r of a vector into the single-right-hand-side internal
+// layout [k][node][t] (plane stride Ps).
+void launch_gather(const Grid& g, const double* vec, int r, double* single, cudaStream_t s);
 
 // Shared-memory limits of the sweep kernels; once per device.
 cudaError_t prepare();

@@ -25,7 +25,7 @@ OPT_SWEEP_THREADS = 7
 EXPORTED = (
     "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
     "lq2d_solve_device", "lq2d_solve_nbjm_device", "lq2d_apply_delta_device", "lq2d_apply_precond_device", "lq2d_apply_delta_static",
-    "lq2d_apply_precond_multi_device",
+    "lq2d_apply_precond_multi_device", "lq2d_solve_multi_device",
     "lq2d_autotune",
     "lq2d_batch_create", "lq2d_batch_solve", "lq2d_batch_destroy", "lq2d_get_solution_device",
     "lq2d_set_option",
@@ -89,6 +89,7 @@ def load() -> ctypes.CDLL:
         "lq2d_apply_delta_device": (i, [_vp, _vp, _vp, _vp]),
         "lq2d_apply_precond_device": (i, [_vp, i, i, _vp, _vp, _vp]),
         "lq2d_apply_precond_multi_device": (i, [_vp, i, i, i, _vp, _vp, _vp]),
+        "lq2d_solve_multi_device": (i, [_vp, i, _vp, ctypes.c_double, i, i, i, _vp, _vp, _vp, _ip, _dp, _vp]),
         "lq2d_autotune": (i, [_vp, i, i, i, _ip, _dp, _vp]),
         "lq2d_apply_delta_static": (i, [i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "lq2d_batch_create": (i, [pp, i, _vp]),
@@ -247,6 +248,18 @@ class Problem:
 
     def apply_precond_device(self, S, L, d_r, d_q, stream=None):
         _check(load().lq2d_apply_precond_device(self._h, S, L, _addr(d_r), _addr(d_q), _stream(stream)))
+
+    def solve_multi_device(self, nrhs, x0s, tol=1e-8, S=2, L=2, max_iter=10000, x=None, u=None, costate=None,
+                           stream=None, allow=(ENOCONV,)):
+        """Solves for nrhs <= 32 initial states x0s [nrhs][K*N][n] (device)
+        at once; returns per-right-hand-side iterations and true relative
+        residuals and the status (tensor-core path, n = 4)."""
+        its = (ctypes.c_int * nrhs)()
+        rel = (ctypes.c_double * nrhs)()
+        code = load().lq2d_solve_multi_device(self._h, nrhs, _addr(x0s), tol, S, L, max_iter, _addr(x), _addr(u),
+                                              _addr(costate), its, rel, _stream(stream))
+        _check(code, allow)
+        return dict(iterations=list(its), rel_residuals=list(rel), status=code)
 
     def apply_precond_multi_device(self, nrhs, S, L, d_r, d_q, stream=None):
         """q_r = D_S r_r for nrhs <= 32 right-hand sides [nrhs][T+1][K*N][n]
