@@ -65,6 +65,9 @@ def parse_args():
                          "K = N = 128, T = 100 family, then time held-out solves from its guess and from zero")
     ap.add_argument("--ws-steps", type=int, default=1500, help="training steps of the warm-start network")
     ap.add_argument("--ws-eval", type=int, default=50, help="held-out instances (seeds 100000+) evaluated")
+    ap.add_argument("--multirhs", type=int, default=0,
+                    help="multi-right-hand-side solve: this many instances of the batch family (K, N in 8..64, "
+                         "T in 50..200), each with 32 initial states x0 ~ N(0, 1), against single solves")
     return ap.parse_args()
 
 
@@ -664,6 +667,97 @@ def run_warmstart(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_multirhs(args, dist):
+    """Many initial states per instance: 32 right-hand sides of each of
+    `args.multirhs` uneven instances solved by lq2d_solve_multi_device
+    (tensor-core preconditioner), against single-right-hand-side solves of
+    the same initial states (FP64 and precision mode 2) on the first
+    instances."""
+    import torch
+
+    from paper_2304_04980_gb300 import lq2d
+
+    lq2d.load()
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    grids = synth.batch_grids(args.multirhs)
+    probs, x0s = [], []
+    for idx, g in enumerate(grids):
+        probs.append(lq2d.Problem.from_grid(g))
+        rng = np.random.default_rng(20000 + idx)
+        x0s.append(torch.from_numpy(rng.standard_normal((32, g.nodes, g.n))).to(dev))
+    for p, x in zip(probs, x0s):
+        p.solve_multi_device(32, x, args.tol, 2, 2, 100000, stream=stream)
+    torch.cuda.synchronize()
+    launches0 = sum(p.stats()["launches_total"] for p in probs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its, worst = 0, 0.0
+    e0.record(stream)
+    for _ in range(args.steps):
+        for p, x in zip(probs, x0s):
+            out = p.solve_multi_device(32, x, args.tol, 2, 2, 100000, stream=stream)
+            its += sum(out["iterations"])
+            worst = max(worst, max(out["rel_residuals"]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    multi_ms = e0.elapsed_time(e1) / args.steps
+    launches = sum(p.stats()["launches_total"] for p in probs) - launches0
+    # single-right-hand-side solves of the same initial states (solve time
+    # only; the data update that sets each x0 is not timed)
+    sub = min(2, len(grids))
+    single = {}
+    for mode in (0, 2):
+        tot_ms, tot_its = 0.0, 0
+        for idx in range(sub):
+            g = grids[idx]
+            sp = lq2d.Problem.from_grid(g)
+            sp.set_precision(mode)
+            sp.solve_device(args.tol, 2, 2, 100000, stream=stream)
+            for r in range(32):
+                arrays = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in g.with_x0(
+                    x0s[idx][r].cpu().numpy()).arrays()]
+                sp.update_device(*arrays, stream=stream)
+                torch.cuda.synchronize()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                o = sp.solve_device(args.tol, 2, 2, 100000, stream=stream)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                tot_ms += a0.elapsed_time(a1)
+                tot_its += o["iterations"]
+            sp.close()
+        single[mode] = (tot_ms, tot_its)
+    # the same instances' share of the multi-right-hand-side time
+    sub_ms = 0.0
+    for idx in range(sub):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        probs[idx].solve_multi_device(32, x0s[idx], args.tol, 2, 2, 100000, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        sub_ms += a0.elapsed_time(a1)
+    rhs = 32 * len(grids)
+    line = {
+        "metric": "multi-right-hand-side time-to-solve at 1e-8 rel residual (right-hand sides/s)",
+        "value": rhs / (multi_ms / 1e3), "unit": "rhs/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": multi_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 iterates, f32 products, tf32 preconditioner", "data": "synthetic",
+        "config": {"workload": "multirhs%d: batch family (K, N in 8..64, T in 50..200, n = 4, m = 2), 32 x0 "
+                               "~ N(0, 1) per instance" % len(grids), "tol": args.tol, "S": 2, "L": 2},
+        "pcg_steps_per_rhs": its / (args.steps * rhs), "max_rel_residual": worst,
+        "single_rhs_first_instances": {
+            "instances": sub, "multi_ms": sub_ms,
+            "fp64_ms": single[0][0], "fp64_steps_per_rhs": single[0][1] / (32 * sub),
+            "mixed2_ms": single[2][0], "mixed2_steps_per_rhs": single[2][1] / (32 * sub),
+            "speedup_vs_fp64": single[0][0] / sub_ms, "speedup_vs_mixed2": single[2][0] / sub_ms},
+        "gpu_launches": launches,
+    }
+    for p in probs:
+        p.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.warmstart > 0:
@@ -671,6 +765,9 @@ def main():
         return
     if args.batch > 0:
         run_batch(args, Dist())
+        return
+    if args.multirhs > 0:
+        run_multirhs(args, Dist())
         return
     dist = Dist()
     if args.impl == "reference":
