@@ -536,19 +536,11 @@ int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   return LQ2D_OK;
 }
 
-int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
-  const bool use_stream = h->driver == 1 || h->timing;
-  if (!use_stream) {
-    cudaGraphExec_t exec;
-    int rc = get_graph(h, S, L, &exec);
-    if (rc) return rc;
-    LQ_CUDA(cudaGraphLaunch(exec, s));
-    h->graph_body_kernels = 2 + sweeps_per_step(h, S, L) + 1;
-    return LQ2D_OK;
-  }
-  // driver 1: steps enqueued from the host in chunks; the stop flag of the
-  // previous chunk is read while the current one runs.  Kernels return at
-  // once when the flag is set, so the overshoot costs only empty launches.
+// Driver 1: steps enqueued from the host in chunks; the stop flag of the
+// previous chunk is read while the current one runs.  Kernels return at
+// once when the flag is set, so the overshoot costs only empty launches.
+template <typename Step>
+int run_host_loop(lq2d_problem* h, int max_iter, cudaStream_t s, Step&& enqueue_one) {
   const int cap = max_iter + 2;
   int enq = 0;
   cudaEvent_t flag_ev[2];
@@ -558,7 +550,7 @@ int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
   bool pending[2] = {false, false};
   int rc = LQ2D_OK;
   while (enq < cap) {
-    for (int c = 0; c < kStreamChunk && enq < cap; ++c, ++enq) enqueue_step(h, S, L, s, h->timing != 0);
+    for (int c = 0; c < kStreamChunk && enq < cap; ++c, ++enq) enqueue_one();
     cudaMemcpyAsync(&h->h_done[slot], &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaEventRecord(flag_ev[slot], s);
     pending[slot] = true;
@@ -575,6 +567,20 @@ int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
   cudaEventDestroy(flag_ev[1]);
   return rc;
 }
+
+int run_loop(lq2d_problem* h, int S, int L, int max_iter, cudaStream_t s) {
+  const bool use_stream = h->driver == 1 || h->timing;
+  if (!use_stream) {
+    cudaGraphExec_t exec;
+    int rc = get_graph(h, S, L, &exec);
+    if (rc) return rc;
+    LQ_CUDA(cudaGraphLaunch(exec, s));
+    h->graph_body_kernels = 2 + sweeps_per_step(h, S, L) + 1;
+    return LQ2D_OK;
+  }
+  return run_host_loop(h, max_iter, s, [&]() { enqueue_step(h, S, L, s, h->timing != 0); });
+}
+
 
 // Sums the event pairs of the timed steps.  Pool order per step: one pair
 // around the Delta apply, then S*L pairs around the sweeps.  Only launches
@@ -1121,6 +1127,8 @@ int ensure_mrhs_solve(lq2d_problem* h) {
 // (S*L sweeps alternate between two buffers; S*L is even).
 float* multi_q(lq2d_problem* h) { return h->m_thB; }
 
+constexpr int kMultiStepKernels = 7;  // besides the S*L sweeps
+
 // One step of the multi-right-hand-side PCG: the product and alpha, the
 // update and tests, the preconditioner, mu and beta, then the residual
 // replacements that are due.
@@ -1131,9 +1139,8 @@ void enqueue_multi_step(lq2d_problem* h, int S, int L, cudaStream_t s) {
   enqueue_precond_multi(h, S, L, h->mv.r32, h->st, s);
   mrhs::launch_mu(g, multi_q(h), h->mv, h->m_partials, h->mstate, h->st, s);
   mrhs::launch_replace(g, h->op64, h->mv, h->m_partials, h->mstate, h->st, false, s);
+  h->launches += kMultiStepKernels;
 }
-
-constexpr int kMultiStepKernels = 7;  // besides the S*L sweeps
 
 int get_multi_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   if (h->m_exec && h->m_graph_S == S && h->m_graph_L == L) {
@@ -1202,10 +1209,16 @@ int solve_multi_impl(lq2d_problem* h, int nrhs, const double* d_x0s, double tol,
     LQ_CUDA(cudaMemsetAsync(h->mv.d, 0, (size_t)mrhs::vec_floats(g) * sizeof(double), s));
     LQ_CUDA(cudaMemsetAsync(h->mv.d32, 0, (size_t)mrhs::vec_floats(g) * sizeof(float), s));
     h->launches += S * L + 1;
-    cudaGraphExec_t exec;
-    rc = get_multi_graph(h, S, L, &exec);
-    if (rc != LQ2D_OK) return rc;
-    LQ_CUDA(cudaGraphLaunch(exec, s));
+    if (h->driver == 1 || h->timing) {
+      // host-enqueued steps (driver 1): every kernel is a launch of its own
+      rc = run_host_loop(h, max_iter, s, [&]() { enqueue_multi_step(h, S, L, s); });
+      if (rc != LQ2D_OK) return rc;
+    } else {
+      cudaGraphExec_t exec;
+      rc = get_multi_graph(h, S, L, &exec);
+      if (rc != LQ2D_OK) return rc;
+      LQ_CUDA(cudaGraphLaunch(exec, s));
+    }
     // the true residual of every right-hand side decides convergence
     mrhs::launch_replace(g, h->op64, h->mv, h->m_partials, h->mstate, h->st, true, s);
     h->launches += 3;

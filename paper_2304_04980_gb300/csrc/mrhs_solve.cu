@@ -5,7 +5,7 @@
 // and the per-right-hand-side scalars (alpha, beta, mu) live in one
 // register per lane.  Reductions are per lane: warp partial sums are added
 // across the CTA through shared memory, one slot per CTA and lane is
-// written, and the last CTA adds the slots in block order (deterministic).
+// written, and the last CTA adds the slots in a fixed order (deterministic).
 //
 // Precision follows precision mode 2 of the single-right-hand-side solver:
 // r, delta and d are FP64; the product Delta d runs in FP32 from an FP32
@@ -24,10 +24,13 @@ namespace mrhs {
 namespace {
 
 constexpr int kWarps = 8;  // warps per CTA of the element-wise kernels
-constexpr int kMaxBlocks = 2048;
+constexpr int kMaxBlocks = 1216;  // 8 per SM of a 152-SM GPU
 
 // Sums NV values per lane over the grid; true in the last CTA's warp 0,
-// whose lane r then holds the totals of right-hand side r in out[].
+// whose lane r then holds the totals of right-hand side r in out[].  The
+// last CTA adds the per-CTA slots with all its warps (warp w takes every
+// kWarps-th CTA, then warp 0 adds the kWarps sums in order), so the result
+// does not depend on the order in which CTAs finish.
 template <int NV>
 __device__ bool rhs_reduce(const double (&v)[NV], double* partials, unsigned int* counter, double (&out)[NV]) {
   __shared__ double red[NV][kWarps][32];
@@ -52,16 +55,24 @@ __device__ bool rhs_reduce(const double (&v)[NV], double* partials, unsigned int
     last = prev == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || wid != 0) return false;
+  if (!last) return false;
   __threadfence();
-  const volatile double* vp = partials;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     double s = 0.0;
-    for (unsigned int b = 0; b < gridDim.x; ++b) s += vp[((size_t)b * NV + j) * 32 + lane];
+#pragma unroll 8
+    for (unsigned int b = wid; b < gridDim.x; b += kWarps) s += __ldcg(&partials[((size_t)b * NV + j) * 32 + lane]);
+    red[j][wid][lane] = s;
+  }
+  __syncthreads();
+  if (wid != 0) return false;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += red[j][w][lane];
     out[j] = s;
   }
-  __syncwarp();
   if (lane == 0) *counter = 0u;
   return true;
 }
