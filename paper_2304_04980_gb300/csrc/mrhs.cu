@@ -39,7 +39,7 @@ namespace {
 
 constexpr int kWpc = 4;                  // warps (time steps) per CTA
 constexpr int kNb = 2;                   // staging buffers
-constexpr int kPs = 40;                  // row stride (floats) of the [rows][32 rhs] panels
+constexpr int kPs = 32;                  // row stride (floats) of the [rows][32 rhs] panels
 constexpr int kRec = 384;                // floats per pair-row record
 constexpr int kW = 256;                  // floats per coupling matrix (4 k-steps of 64)
 
@@ -64,30 +64,37 @@ __device__ __forceinline__ void cp16z(float* smem, const float* gmem, bool valid
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
 }
 
+// Panels P[row][rhs] are stored with a swizzle: element (row, col) sits at
+// row * kPs + (col ^ swz(row)).  It moves whole 8-float groups, so 16-byte
+// chunks stay contiguous, and it spreads the four rows an A fragment reads
+// at once (rows c0 + q, q = 0..3) over all 32 banks.
+__device__ __forceinline__ int swz(int row) { return (row & 3) << 3; }
+__device__ __forceinline__ int pidx(int row, int col) { return row * kPs + (col ^ swz(row)); }
+
 // A fragment (16 rhs x 8 columns) of right-hand-side tile `tile` from a
-// panel P[col][rhs] (row stride kPs), with columns c0 .. c0+7.
+// panel P[col][rhs], with columns c0 .. c0+7 (c0 a multiple of 8).
 __device__ __forceinline__ void a_frag(const float* P, int c0, int tile, int g, int q, unsigned (&a)[4]) {
   const int m = g + 16 * tile;
-  a[0] = tf32_bits(P[(c0 + q) * kPs + m]);
-  a[1] = tf32_bits(P[(c0 + q) * kPs + m + 8]);
-  a[2] = tf32_bits(P[(c0 + q + 4) * kPs + m]);
-  a[3] = tf32_bits(P[(c0 + q + 4) * kPs + m + 8]);
+  a[0] = tf32_bits(P[pidx(c0 + q, m)]);
+  a[1] = tf32_bits(P[pidx(c0 + q, m + 8)]);
+  a[2] = tf32_bits(P[pidx(c0 + q + 4, m)]);
+  a[3] = tf32_bits(P[pidx(c0 + q + 4, m + 8)]);
 }
 
 // D fragment of tile `tile` to / from a panel P[row][rhs].
 __device__ __forceinline__ void d_store(float* P, int tile, int g, int q, const float (&d)[4]) {
   const int m = g + 16 * tile;
-  P[(2 * q) * kPs + m] = d[0];
-  P[(2 * q + 1) * kPs + m] = d[1];
-  P[(2 * q) * kPs + m + 8] = d[2];
-  P[(2 * q + 1) * kPs + m + 8] = d[3];
+  P[pidx(2 * q, m)] = d[0];
+  P[pidx(2 * q + 1, m)] = d[1];
+  P[pidx(2 * q, m + 8)] = d[2];
+  P[pidx(2 * q + 1, m + 8)] = d[3];
 }
 __device__ __forceinline__ void d_load(const float* P, int tile, int g, int q, float (&d)[4]) {
   const int m = g + 16 * tile;
-  d[0] = P[(2 * q) * kPs + m];
-  d[1] = P[(2 * q + 1) * kPs + m];
-  d[2] = P[(2 * q) * kPs + m + 8];
-  d[3] = P[(2 * q + 1) * kPs + m + 8];
+  d[0] = P[pidx(2 * q, m)];
+  d[1] = P[pidx(2 * q + 1, m)];
+  d[2] = P[pidx(2 * q, m + 8)];
+  d[3] = P[pidx(2 * q + 1, m + 8)];
 }
 
 // Writes an 8 x 32 panel P[a][rhs] (pair-row unknown a = jj*4 + k) to a
@@ -100,19 +107,25 @@ __device__ __forceinline__ void panel_to_global(float* vec, const float* P, long
 #pragma unroll
   for (int jj = 0; jj < 2; ++jj) {
     if (jj == 1 && !two) continue;
-    const float4 val = *reinterpret_cast<const float4*>(P + (4 * jj + k) * kPs + ch * 4);
+    const float4 val = *reinterpret_cast<const float4*>(P + pidx(4 * jj + k, ch * 4));
     *reinterpret_cast<float4*>(vec + k * plane + pt0 + jj * node_step + ch * 4) = val;
   }
 }
 
-template <int NW>
+// Shared-memory layout of variant VAR.  The neighbour panels are time
+// slices shared by the CTA's warps: slice s holds time t0 - 1 + s for the
+// Xi~ sweep (kWpc + 2 slices; warp w reads slices w and w + 2, i.e. t - 1
+// and t + 1) and t0 + s for the Omega~ sweep (kWpc slices).
+template <int VAR>
 struct Layout {
+  static constexpr int NW = VAR == 0 ? 0 : (VAR == 1 ? 1 : 2);   // coupling matrices
+  static constexpr int NSL = VAR == 0 ? 0 : (VAR == 1 ? kWpc : kWpc + 2);  // neighbour slices
   // offsets in floats of the dynamic shared memory
   static constexpr int rec = 0;                                   // [kNb][3][kRec]
   static constexpr int w = rec + kNb * 3 * kRec;                  // [kNb][NW][kW]
   static constexpr int src = w + kNb * NW * kW;                   // [kNb][kWpc][8][kPs]
-  static constexpr int halo = src + kNb * kWpc * 8 * kPs;         // [kNb][kWpc][NW][32][kPs]
-  static constexpr int ring = halo + kNb * kWpc * NW * 32 * kPs;  // [kWpc][3][8][kPs]
+  static constexpr int halo = src + kNb * kWpc * 8 * kPs;         // [kNb][NSL][32][kPs]
+  static constexpr int ring = halo + kNb * NSL * 32 * kPs;        // [kWpc][3][8][kPs]
   static constexpr int xch = ring + kWpc * 3 * 8 * kPs;           // [kWpc][8][kPs]
   static constexpr int total = xch + kWpc * 8 * kPs;
 };
@@ -134,8 +147,8 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
                                                                float* __restrict__ rth_out,
                                                                const SolverState* __restrict__ st) {
   if (st != nullptr && st->done) return;
-  constexpr int NW = VAR == 0 ? 0 : (VAR == 1 ? 1 : 2);
-  using Ly = Layout<NW>;
+  using Ly = Layout<VAR>;
+  constexpr int NW = Ly::NW, NSL = Ly::NSL;
   extern __shared__ __align__(16) float smf[];
   const int Tp = g.T + 1;
   const int tiles = (Tp + kWpc - 1) / kWpc;
@@ -155,29 +168,33 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
   const int lk = lane >> 3, lch = lane & 7;
   const long long own0 = (long long)lk * plane + ((long long)j0 * Tp + t) * kRhs + lch * 4;  // pair-row 0, jj = 0
 
-  // halo rows (h, c = lk) of the eight staged neighbours: node offset from
-  // the pair's first node (j0) of pair-row 0, and which of them exist
-  long long hoff[8];
-  unsigned col_ok = 0u, above = 0u, below = 0u;
+  // neighbour rows staged by this thread: rows hr[x] = tid / 8 + 16 x of
+  // every slice (row = 4 h + c for staged node h, component c), chunk
+  // tid % 8; node offset from the pair's first node of pair-row 0, and
+  // whether the node exists
+  const int hch = tid & 7;
+  int hr[2];
+  long long hoff[2];
+  bool hcol[2], hup[2], hdn[2];
   if (NW > 0) {
     const unsigned long long packed = VAR == 2 ? hot::kXiPacked : hot::kOmPacked;
 #pragma unroll
-    for (int h = 0; h < 8; ++h) {
+    for (int x = 0; x < 2; ++x) {
+      hr[x] = (tid >> 3) + 16 * x;
+      const int h = hr[x] >> 2, c = hr[x] & 3;
       const unsigned code = (unsigned)((packed >> (5 * h)) & 31ull);
       const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
-      if (jn >= 0 && jn < g.N) col_ok |= 1u << h;
-      if (di < 0) above |= 1u << h;
-      if (di > 0) below |= 1u << h;
-      hoff[h] = (long long)lk * plane + ((long long)(di * g.N + jn) * Tp) * kRhs + lch * 4;
+      hcol[x] = jn >= 0 && jn < g.N;
+      hup[x] = di < 0;
+      hdn[x] = di > 0;
+      hoff[x] = (long long)c * plane + ((long long)(di * g.N + jn) * Tp) * kRhs + hch * 4;
     }
   }
-  // time slices of the halo panels and whether they exist (warp-uniform)
-  int tn[2] = {t, t};
+  // whether this warp's coupling terms exist (warp-uniform): Omega~ is zero
+  // at t = 0; Xi~ takes t - 1 for t >= 1 and t + 1 for t < T
   bool tok[2] = {false, false};
   if (VAR == 1) tok[0] = active && t >= 1;
   if (VAR == 2) {
-    tn[0] = t - 1;
-    tn[1] = t + 1;
     tok[0] = active && t >= 1;
     tok[1] = active && t < g.T;
   }
@@ -202,21 +219,20 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
 #pragma unroll
     for (int jj = 0; jj < 2; ++jj) {
       const bool ok = active && (jj == 0 || two);
-      cp16z(smf + Ly::src + ((b * kWpc + w) * 8 + 4 * jj + lk) * kPs + lch * 4,
+      cp16z(smf + Ly::src + (b * kWpc + w) * 8 * kPs + pidx(4 * jj + lk, lch * 4),
             pv + (ok ? own0 + rb + jj * node_step : 0), ok);
     }
     if (fwd && NW > 0) {
-      unsigned rows = col_ok;
-      if (i < 1) rows &= ~above;
-      if (i + 1 >= g.K) rows &= ~below;
 #pragma unroll
-      for (int qq = 0; qq < NW; ++qq) {
-        float* dst = smf + Ly::halo + (((b * kWpc + w) * NW + qq) * 32 + lk) * kPs + lch * 4;
-        const long long tb = rb + (long long)tn[qq] * kRhs;
+      for (int sl = 0; sl < NSL; ++sl) {
+        const int tn = t0 + sl - (VAR == 2 ? 1 : 0);
+        const bool t_ok = tn >= 0 && tn <= g.T;
+        const long long tb = rb + (long long)tn * kRhs;
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          const bool ok = tok[qq] && ((rows >> h) & 1u);
-          cp16z(dst + 4 * h * kPs, th_in + (ok ? hoff[h] + tb : 0), ok);
+        for (int x = 0; x < 2; ++x) {
+          const bool ok = t_ok && hcol[x] && !(hup[x] && i < 1) && !(hdn[x] && i + 1 >= g.K);
+          cp16z(smf + Ly::halo + (b * NSL + sl) * 32 * kPs + pidx(hr[x], hch * 4), th_in + (ok ? hoff[x] + tb : 0),
+                ok);
         }
       }
     }
@@ -244,7 +260,7 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
 #pragma unroll
       for (int qq = 0; qq < NW; ++qq) {
         if (!tok[qq]) continue;
-        const float* H = smf + Ly::halo + ((b * kWpc + w) * NW + qq) * 32 * kPs;
+        const float* H = smf + Ly::halo + (b * NSL + w + 2 * qq) * 32 * kPs;
         const float* W = smf + Ly::w + (b * NW + qq) * kW;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -466,7 +482,7 @@ __global__ void transpose_kernel(Grid g, int nrhs, const FT* __restrict__ in, TT
 
 template <int VAR>
 size_t smem_bytes() {
-  return (size_t)Layout<VAR == 0 ? 0 : (VAR == 1 ? 1 : 2)>::total * sizeof(float);
+  return (size_t)Layout<VAR>::total * sizeof(float);
 }
 
 }  // namespace

@@ -140,7 +140,7 @@ __global__ void init_kernel(Grid g, int nrhs, const double* __restrict__ x0s, co
 // z = Q~^-1 A~' dn (see delta_z_kernel): FP32 in the loop with dn = q + beta
 // d32, FP64 for a replacement with dn = delta.
 template <typename CT, bool LOOP>
-__global__ void z_kernel(Grid g, OpData<CT> op, const float* __restrict__ q, const float* __restrict__ d32,
+__global__ void __launch_bounds__(kWarps * 32, 3) z_kernel(Grid g, OpData<CT> op, const float* __restrict__ q, const float* __restrict__ d32,
                          const double* __restrict__ delta, CT* __restrict__ z, const State* ms,
                          const SolverState* st, int force) {
   if (LOOP && st->done) return;
@@ -161,19 +161,26 @@ __global__ void z_kernel(Grid g, OpData<CT> op, const float* __restrict__ q, con
 #pragma unroll
     for (int k = 0; k < kN; ++k) w[k] = -dn_at(k, it);
     if (t < g.T) {
+      // every neighbour's values are loaded before any is used, so that the
+      // loads of the five directions are in flight together (an absent
+      // neighbour reads the node's own row and is skipped below)
+      int rn[5];
+      CT dv[5][kN];
 #pragma unroll
       for (int dir = 0; dir < 5; ++dir) {
-        const int rn = nbr_node(i, j, dir, g.K, g.N);
-        if (rn < 0) continue;
-        const CT* blk = hot::ahat_col<kN>(op, rn, dir);
-        const long long rpt = (long long)rn * Tp + t + 1;
-        CT dv[kN];
+        rn[dir] = nbr_node(i, j, dir, g.K, g.N);
+        const long long rpt = (long long)(rn[dir] >= 0 ? rn[dir] : p) * Tp + t + 1;
 #pragma unroll
-        for (int c = 0; c < kN; ++c) dv[c] = dn_at(c, rpt);
+        for (int c = 0; c < kN; ++c) dv[dir][c] = dn_at(c, rpt);
+      }
+#pragma unroll
+      for (int dir = 0; dir < 5; ++dir) {
+        if (rn[dir] < 0) continue;
+        const CT* blk = hot::ahat_col<kN>(op, rn[dir], dir);
 #pragma unroll
         for (int c = 0; c < kN; ++c)
 #pragma unroll
-          for (int k = 0; k < kN; ++k) w[k] += blk[c * kN + k] * dv[c];
+          for (int k = 0; k < kN; ++k) w[k] += blk[c * kN + k] * dv[dir][c];
       }
     }
     const CT* Qb = (t == g.T ? op.QTi : op.Qi) + (size_t)p * kN * kN;
@@ -192,7 +199,7 @@ __global__ void z_kernel(Grid g, OpData<CT> op, const float* __restrict__ q, con
 // and alpha = mu / (y' dn) set (0 for frozen right-hand sides).
 // Replacement: dn = delta, y in FP64.
 template <typename CT, bool LOOP>
-__global__ void y_kernel(Grid g, OpData<CT> op, const CT* __restrict__ z, const float* __restrict__ q, SolveVecs v,
+__global__ void __launch_bounds__(kWarps * 32, 3) y_kernel(Grid g, OpData<CT> op, const CT* __restrict__ z, const float* __restrict__ q, SolveVecs v,
                          double* partials, State* ms, SolverState* st, int force) {
   if (LOOP && st->done) return;
   if (!LOOP && !force && (st->done || !ms->any_repl)) return;
@@ -213,19 +220,24 @@ __global__ void y_kernel(Grid g, OpData<CT> op, const CT* __restrict__ z, const 
       yk[k] = -z[e];
     }
     if (t >= 1) {
+      // neighbour loads first (see z_kernel)
+      int rn[5];
+      CT zv[5][kN];
 #pragma unroll
       for (int dir = 0; dir < 5; ++dir) {
-        const int rn = nbr_node(i, j, dir, g.K, g.N);
-        if (rn < 0) continue;
-        const CT* blk = hot::ahat_row<kN>(op, p, dir);
-        const long long rpt = (long long)rn * Tp + t - 1;
-        CT zv[kN];
+        rn[dir] = nbr_node(i, j, dir, g.K, g.N);
+        const long long rpt = (long long)(rn[dir] >= 0 ? rn[dir] : p) * Tp + t - 1;
 #pragma unroll
-        for (int c = 0; c < kN; ++c) zv[c] = z[vidx(g, plane, c, rpt) + lane];
+        for (int c = 0; c < kN; ++c) zv[dir][c] = z[vidx(g, plane, c, rpt) + lane];
+      }
+#pragma unroll
+      for (int dir = 0; dir < 5; ++dir) {
+        if (rn[dir] < 0) continue;
+        const CT* blk = hot::ahat_row<kN>(op, p, dir);
 #pragma unroll
         for (int k = 0; k < kN; ++k)
 #pragma unroll
-          for (int c = 0; c < kN; ++c) yk[k] += blk[k * kN + c] * zv[c];
+          for (int c = 0; c < kN; ++c) yk[k] += blk[k * kN + c] * zv[dir][c];
       }
       const CT* S = op.Sb + (size_t)p * kN * kN;
 #pragma unroll
