@@ -201,7 +201,7 @@ int lq2d_apply_precond_device(lq2d_problem *h, int outer_S, int inner_L, const v
  *   nrhs       1..32
  *   d_r, d_q   device buffers [nrhs][T+1][K*N][n] (FP64), right-hand side
  *              r of index i at d_r + i (T+1) K N n
- * Needs n = 4 (LQ2D_EINVAL otherwise).  The first call allocates the
+ * Needs n = 4 and T + 1 <= 65535 (LQ2D_EINVAL otherwise).  The first call allocates the
  * operands of this path (about 16 (T+1) K N n bytes per vector, four
  * vectors, plus the rearranged factors) and every setup invalidates them;
  * they are rebuilt on the next call.  Returns after the work on `stream`

@@ -1437,6 +1437,7 @@ int lq2d_apply_precond_multi_device(lq2d_problem* h, int nrhs, int S, int L, con
   if (nrhs < 1 || nrhs > mrhs::kRhs) return fail(LQ2D_EINVAL, "nrhs must be in 1..32");
   if (S < 1) return fail(LQ2D_EINVAL, "outer_S must be >= 1");
   if (L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "inner_L must be even and >= 2");
+  if (h->g.T + 1 > 65535) return fail(LQ2D_EINVAL, "the layout transposes need T + 1 <= 65535");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = ensure_mrhs(h, s);
   if (rc != LQ2D_OK) return rc;
