@@ -65,6 +65,9 @@ def parse_args():
                          "K = N = 128, T = 100 family, then time held-out solves from its guess and from zero")
     ap.add_argument("--ws-steps", type=int, default=1500, help="training steps of the warm-start network")
     ap.add_argument("--ws-eval", type=int, default=50, help="held-out instances (seeds 100000+) evaluated")
+    ap.add_argument("--ws-group", type=int, default=32,
+                    help="training pairs per multi-right-hand-side solve (seeds sharing one coupling value); "
+                         "1 = one mixed-precision solve per pair")
     ap.add_argument("--multirhs", type=int, default=0,
                     help="multi-right-hand-side solve: this many instances of the batch family (K, N in 8..64, "
                          "T in 50..200), each with 32 initial states x0 ~ N(0, 1), against single solves")
@@ -601,7 +604,10 @@ def run_warmstart(args, dist):
     torch.cuda.set_device(dev)
     fam = synth.warmstart_family()
     ws = warmstart.WarmStart(fam, channels=64, layers=6, batch=8, seed=0, device=str(dev))
-    gen_s = ws.generate(range(1000, 1000 + args.warmstart), tol=1e-6, precision=1)
+    if args.ws_group > 1:
+        gen_s = ws.generate_grouped(range(1000, 1000 + args.warmstart), tol=1e-6, group=args.ws_group)
+    else:
+        gen_s = ws.generate(range(1000, 1000 + args.warmstart), tol=1e-6, precision=1)
     sigma = float(ws.targets.std())
     ws.net.close()
     ws.net = lq2d.WarmStartNet(fam.K, fam.N, fam.T, fam.n, 64, 6, 8, sigma)
@@ -620,8 +626,10 @@ def run_warmstart(args, dist):
         ws.solve(99999, tol=args.tol, warm=warm, precision=prec)
     its = {k: [] for k, _, _ in combos}
     secs = {k: [] for k, _, _ in combos}
-    errs = []
+    errs, guess_errs = [], []
     for seed in range(100000, 100000 + args.ws_eval):
+        c, x0 = fam.instance_params(seed)
+        guess = ws.guess(c, torch.from_numpy(x0).to(dev))
         ref = None
         for key, warm, prec in combos:
             r = ws.solve(seed, tol=args.tol, warm=warm, precision=prec)
@@ -629,6 +637,7 @@ def run_warmstart(args, dist):
             secs[key].append(r["seconds"])
             if ref is None:
                 ref = r["costate"]
+                guess_errs.append(float(torch.linalg.norm(guess - ref) / torch.linalg.norm(ref)))
             else:
                 errs.append(float(torch.linalg.norm(r["costate"] - ref) / torch.linalg.norm(ref)))
     zero_it, warm_it, zero_s, warm_s = its["zero"], its["warm"], secs["zero"], secs["warm"]
@@ -650,10 +659,13 @@ def run_warmstart(args, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16 weights / f32 net", "data": "synthetic",
         "config": {"workload": "warmstart K = N = 128, n = 4, m = 2, T = 100, coupling 0.02..0.2, x0 ~ N(0, 1)",
                    "train_instances": args.warmstart, "train_steps": args.ws_steps, "batch": 8,
+                   "train_generation": ("multi-right-hand-side solves at tol 1e-6, %d seeds per coupling value"
+                                        % args.ws_group if args.ws_group > 1 else "mixed-precision solves at tol 1e-6"),
                    "net": "6 x conv3x3, 64 channels, 404 outputs", "eval_instances": args.ws_eval, "tol": args.tol},
         "zero_start_ms": zero_ms, "speedup_vs_zero_start": zero_ms / warm_ms,
         "iterations_zero": float(np.mean(zero_it)), "iterations_warm": float(np.mean(warm_it)),
         "max_rel_diff_vs_zero_fp64": max(errs), "guess_ms": guess_ms,
+        "guess_rel_err_heldout": float(np.mean(guess_errs)),
         "mixed": {"zero_start_ms": 1e3 * float(np.mean(secs["zero_mixed"])),
                   "warm_start_ms": 1e3 * float(np.mean(secs["warm_mixed"])),
                   "iterations_zero": float(np.mean(its["zero_mixed"])),

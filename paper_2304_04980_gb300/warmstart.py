@@ -72,6 +72,35 @@ class WarmStart:
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
+    def generate_grouped(self, seeds, tol: float = 1e-6, S: int = 2, L: int = 2, group: int = 32):
+        """As generate, 32 instances per solve: consecutive seeds form groups
+        of `group` that share the coupling drawn by the group's first seed
+        (each keeps its own x0), and each group is one multi-right-hand-side
+        solve (lq2d_solve_multi_device).  The pairs still cover the family:
+        c is uniform over groups, x0 standard normal per pair.  Returns the
+        wall time."""
+        torch = _torch()
+        f = self.family
+        seeds = list(seeds)
+        count = len(seeds)
+        self.x0 = torch.empty((count, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.targets = torch.empty((count, f.T + 1, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.couplings = np.empty(count)
+        self.iterations = np.empty(count, dtype=np.int64)
+        t0 = time.perf_counter()
+        for start in range(0, count, group):
+            idx = list(range(start, min(start + group, count)))
+            c = f.instance_params(seeds[idx[0]])[0]
+            for k in idx:
+                self.x0[k].copy_(torch.from_numpy(f.instance_params(seeds[k])[1]))
+                self.couplings[k] = c
+            prob = self._problem_for(f.grid(c, f.instance_params(seeds[idx[0]])[1]))
+            out = prob.solve_multi_device(len(idx), self.x0[idx[0]:idx[-1] + 1], tol, S, L, 100000,
+                                          costate=self.targets[idx[0]:idx[-1] + 1])
+            self.iterations[idx[0]:idx[-1] + 1] = out["iterations"]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
     # -- training --------------------------------------------------------
     def fit(self, steps: int, lr: float = 1e-3, lr_final: float = 1e-4, seed: int = 0, log_every: int = 0):
         """Adam steps on random minibatches of the generated pairs, with the

@@ -164,3 +164,26 @@ def test_trained_network_reduces_iterations(dev):
         warm_its.append(w["iterations"])
     assert np.mean(warm_its) < np.mean(zero_its)
     ws.close()
+
+
+def test_grouped_generation_matches_the_oracle(dev):
+    """Training pairs from multi-right-hand-side solves: groups of 16
+    consecutive seeds (the last one ragged) share the coupling of the group's
+    first seed, each pair keeps its own x0, and every target is that
+    instance's costate."""
+    from paper_2304_04980_gb300 import warmstart
+    fam = synth.warmstart_family(8, 6, 9, 4, 2, seed=12)
+    ws = warmstart.WarmStart(fam, channels=8, layers=2, batch=4, seed=0)
+    seeds = list(range(2000, 2040))
+    ws.generate_grouped(seeds, tol=1e-10, group=16)
+    for k in (0, 15, 16, 31, 39):
+        c = fam.instance_params(seeds[k - k % 16])[0]
+        x0 = fam.instance_params(seeds[k])[1]
+        assert ws.couplings[k] == c
+        assert np.array_equal(ws.x0[k].cpu().numpy(), x0)
+        g = fam.grid(c, x0)
+        ref = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())).solve(1e-12).delta
+        got = ws.targets[k].cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref)
+    assert np.all(ws.iterations > 0)
+    ws.close()
