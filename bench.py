@@ -170,7 +170,9 @@ class Clocks:
 def band_solve_flops(K, n, cols):
     """Forward plus backward substitution with the banded block-Cholesky
     factor of one Phi_bar_{v,t} block (Section IV-B), envelope entries only:
-    each multiply-add counts 2 flops, each diagonal scaling 1."""
+    each multiply-add counts 2 flops, each diagonal scaling 1.  This is the
+    algorithmic count whatever form the kernel stores the factor in; the
+    sweeps' unit-factor form (dense F2 and D^-1 blocks) executes 7-13% more."""
     f = 0
     for i in range(K):
         for a in range(cols * n):

@@ -257,19 +257,22 @@ __global__ void setup_omega_kernel(SetupBuffers sb, int K, int N, int n) {
 //   L2_i = A_{i,i-2} L0_{i-2}^-T
 //   L1_i = (A_{i,i-1} - L2_i L1_{i-1}') L0_{i-1}^-T
 //   L0_i L0_i' = A_{i,i} - L1_i L1_i' - L2_i L2_i'
-// The diagonal factors are stored inverted.  A missing second column (odd N)
-// is carried as a decoupled identity block, whose solution is zero.
-// The substitutions are stored pre-multiplied by the inverted pivots, so
-// that each step of a sweep is one product with the known right-hand side
-// plus products with the two previous results:
-//   forward  (L y = tau):   y_i = L0_i^-1 tau_i - M1_i y_{i-1} - M2_i y_{i-2},
-//                           M1_i = L0_i^-1 L1_i,  M2_i = L0_i^-1 L2_i
-//   backward (L' x = y):    x_i = L0_i^-T y_i - N1_i x_{i+1} - N2_i x_{i+2},
-//                           N1_i = L0_i^-T L1_{i+1}',  N2_i = L0_i^-T L2_{i+2}'
-// (N1, N2 are zero past the last pair-row).  Record of pair-row i (G2 = 2n,
-// blocks G2 x G2 row-major, so a lane's row is contiguous):
-//   [N2_i][N1_i][L0_i^-T]   (backward step i)
-//   [M2_i][M1_i][L0_i^-1]   (forward step i)
+// A missing second column (odd N) is carried as a decoupled identity block,
+// whose solution is zero.  The sweeps use the same factorisation with the
+// pivots taken out, Phi_bar = F D F' with F unit block lower triangular:
+//   F1_i = L1_i L0_{i-1}^-1,  F2_i = L2_i L0_{i-2}^-1,  D_i^-1 = L0_i^-T L0_i^-1
+//   forward  (F y = tau):        y_i = tau_i - F2_i y_{i-2} - F1_i y_{i-1}
+//   backward (F' x = D^-1 y):    x_i = D_i^-1 y_i - N2_i x_{i+2} - N1_i x_{i+1},
+//                                N1_i = F1_{i+1}',  N2_i = F2_{i+2}'
+// (N1, N2 are zero past the last pair-row).  Against the pre-multiplied
+// Cholesky form (y_i = L0_i^-1 tau_i - ...) the forward step loses its
+// product with the pivot, one of six 2n x 2n products per pair-row.
+// Record of pair-row i (G2 = 2n, blocks G2 x G2 row-major, so a lane's row
+// is contiguous):
+//   [N2_i][N1_i][D_i^-1]   (backward step i)
+//   [F2_i][F1_i][L0_i^-1]  (forward step i; the sweeps read F2 and F1, the
+//                           multi-right-hand-side path applies D_i^-1 as
+//                           L0_i^-T L0_i^-1 in TF32)
 __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V, long long fac_rec,
                                     long long fac_vc, int* status) {
   extern __shared__ double smem[];
@@ -370,26 +373,31 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       }
       __syncwarp();
     }
-    // --- backward blocks of the two previous records, now that L1_i and
-    //     L2_i exist: N1_{i-1} = L0_{i-1}^-T L1_i', N2_{i-2} = L0_{i-2}^-T L2_i'
+    // --- F1_i = L1_i L0_{i-1}^-1 and F2_i = L2_i L0_{i-2}^-1, into the
+    //     slots of A_{i,i-1} and A_{i,i-2} (no longer needed)
+    double* F1 = Aim1;
+    double* F2 = Aim2;
+    for (int e = lane; e < BS; e += 32) {
+      const int a = e / G2, b = e % G2;
+      double s1 = 0.0, s2 = 0.0;
+      for (int c = 0; c < G2; ++c) {
+        if (i >= 1) s1 += L1[a * G2 + c] * L0m1[c * G2 + b];
+        if (i >= 2) s2 += L2[a * G2 + c] * L0m2[c * G2 + b];
+      }
+      F1[e] = s1;
+      F2[e] = s2;
+    }
+    __syncwarp();
+    // --- backward blocks of the two previous records, now that F1_i and
+    //     F2_i exist: N1_{i-1} = F1_i', N2_{i-2} = F2_i'
     double* rec_base = sb.fac + (size_t)vc * fac_vc;
     if (i >= 1) {
       double* rp = rec_base + (size_t)(i - 1) * fac_rec;
-      for (int e = lane; e < BS; e += 32) {
-        const int a = e / G2, b = e % G2;
-        double s = 0.0;
-        for (int c = 0; c < G2; ++c) s += L0m1[c * G2 + a] * L1[b * G2 + c];
-        rp[1 * BS + e] = s;
-      }
+      for (int e = lane; e < BS; e += 32) rp[1 * BS + e] = F1[(e % G2) * G2 + e / G2];
     }
     if (i >= 2) {
       double* rp = rec_base + (size_t)(i - 2) * fac_rec;
-      for (int e = lane; e < BS; e += 32) {
-        const int a = e / G2, b = e % G2;
-        double s = 0.0;
-        for (int c = 0; c < G2; ++c) s += L0m2[c * G2 + a] * L2[b * G2 + c];
-        rp[0 * BS + e] = s;
-      }
+      for (int e = lane; e < BS; e += 32) rp[0 * BS + e] = F2[(e % G2) * G2 + e / G2];
     }
     __syncwarp();
     // --- L0^-1 into the slot of pair-row i-2 (no longer needed); lane c
@@ -410,16 +418,14 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
     double* rec = rec_base + (size_t)i * fac_rec;
     for (int e = lane; e < BS; e += 32) {
       const int a = e / G2, b = e % G2;
-      double m1 = 0.0, m2 = 0.0;
-      for (int c = 0; c <= a; ++c) {
-        m1 += L0i[a * G2 + c] * L1[c * G2 + b];
-        m2 += L0i[a * G2 + c] * L2[c * G2 + b];
-      }
+      // D_i^-1 = L0_i^-T L0_i^-1 (L0^-1 is lower triangular)
+      double dinv = 0.0;
+      for (int c = (a > b ? a : b); c < G2; ++c) dinv += L0i[c * G2 + a] * L0i[c * G2 + b];
       rec[0 * BS + e] = 0.0;
       rec[1 * BS + e] = 0.0;
-      rec[2 * BS + e] = L0i[b * G2 + a];
-      rec[3 * BS + e] = m2;
-      rec[4 * BS + e] = m1;
+      rec[2 * BS + e] = dinv;
+      rec[3 * BS + e] = F2[e];
+      rec[4 * BS + e] = F1[e];
       rec[5 * BS + e] = L0i[e];
       prevL1[e] = L1[e];
     }

@@ -21,14 +21,19 @@
 // Results leave the D layout through a shared-memory panel [8 rows][32 rhs],
 // from which the next product reads its A fragment.
 //
-// The factor record of a pair-row holds six blocks (forward and backward
-// substitution with the pivots pre-multiplied, as in the single-RHS sweep):
-//   0: -N2  1: -N1  2: L0^-T  (backward: x_i = L0^-T y_i - N2 x_{i+2} - N1 x_{i+1})
-//   3: -M2  4: -M1  5: L0^-1  (forward:  y_i = L0^-1 tau_i - M2 y_{i-2} - M1 y_{i-1})
+// The factor record of a pair-row holds six blocks (the unit block factor F
+// of Phi_bar = F D F', as in the single-RHS sweep, with the pivot inverse
+// D^-1 = L0^-T L0^-1 kept as its two triangular factors):
+//   0: -N2  1: -N1  2: L0^-T   (backward: x_i = L0^-T z_i - N2 x_{i+2} - N1 x_{i+1})
+//   3: -F2  4: -F1  5: L0^-1   (forward:  y_i = tau_i - F2 y_{i-2} - F1 y_{i-1},
+//                                         z_i = L0^-1 y_i)
 // each stored as B fragments, lane-major: element 2*lane + k of a block is
-// b_k of that lane.  Class 2 is t = 0, where Phi_bar = Q^-1 node by node:
-// its forward block 5 is blkdiag(Q, Q) of the pair's two nodes and the
-// other forward blocks are zero (the backward pass is skipped at t = 0).
+// b_k of that lane.  In TF32 the two triangular products keep the rounding
+// error at the condition number of L0, where one product with D^-1 would
+// take that of D, its square.  The forward step starts from tau's
+// accumulator.  Class 2 is t = 0, where Phi_bar = Q^-1 node by node: there
+// block 5 is blkdiag(Q, Q) of the pair's two nodes, y = Q tau is final and
+// the other forward blocks are zero (the backward pass is skipped at t = 0).
 #include "mrhs.h"
 #include "sweep_tiled.cuh"
 
@@ -274,21 +279,29 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
         }
       }
     }
-    // tau to the exchange panel, then y = L0^-1 tau - M2 y_{i-2} - M1 y_{i-1}
+    // tau to the exchange panel, then y = tau - F2 y_{i-2} - F1 y_{i-1}
+    // (at t = 0, y = Q tau), z = L0^-1 y
     d_store(xch, 0, gq, q, d[0]);
     d_store(xch, 1, gq, q, d[1]);
     __syncwarp();
     if (VAR == 2) panel_to_global(rth_out, xch, plane, pt0, node_step, two, lane);
     const float* R = smf + Ly::rec + (b * 3 + cls) * kRec;
-    float y[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    {
+    float y[2][4];
+    if (cls == 2) {
       const float2 bw = *reinterpret_cast<const float2*>(R + 5 * 64 + 2 * lane);
 #pragma unroll
       for (int tile = 0; tile < 2; ++tile) {
         unsigned a[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y[tile][e] = 0.f;
         a_frag(xch, 0, tile, gq, q, a);
         mma_tf32(y[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
       }
+    } else {
+#pragma unroll
+      for (int tile = 0; tile < 2; ++tile)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y[tile][e] = d[tile][e];
     }
     if (i >= 2 && cls != 2) {
       const float* Y2 = ring + ((i - 2) % 3) * 8 * kPs;
@@ -314,7 +327,26 @@ __global__ void __launch_bounds__(kWpc * 32) mrhs_sweep_kernel(Grid g, Buffers b
     d_store(Y0, 0, gq, q, y[0]);
     d_store(Y0, 1, gq, q, y[1]);
     __syncwarp();
-    panel_to_global(th_out, Y0, plane, pt0, node_step, two, lane);
+    if (cls == 2) {
+      panel_to_global(th_out, Y0, plane, pt0, node_step, two, lane);
+    } else {
+      // z = L0^-1 y, the first half of D^-1 = L0^-T L0^-1, is what the
+      // backward step reads
+      float z[2][4];
+      const float2 bw = *reinterpret_cast<const float2*>(R + 5 * 64 + 2 * lane);
+#pragma unroll
+      for (int tile = 0; tile < 2; ++tile) {
+        unsigned a[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z[tile][e] = 0.f;
+        a_frag(Y0, 0, tile, gq, q, a);
+        mma_tf32(z[tile], a, __float_as_uint(bw.x), __float_as_uint(bw.y));
+      }
+      d_store(xch, 0, gq, q, z[0]);
+      d_store(xch, 1, gq, q, z[1]);
+      __syncwarp();
+      panel_to_global(th_out, xch, plane, pt0, node_step, two, lane);
+    }
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
@@ -387,7 +419,9 @@ __global__ void mrhs_records_kernel(Grid g, NodeData nd, float* rec) {
       double val = 0.0;
       if (cls < 2) {
         const double* blk = nd.fac + (size_t)(2 * v + cls) * nd.fac_vc + (size_t)i * nd.fac_rec + bk * 64;
-        val = blk[row * 8 + col];
+        // block 2 is L0^-T, the transpose of block 5 (the record's D^-1
+        // serves the single-RHS sweep)
+        val = bk == 2 ? blk[3 * 64 + col * 8 + row] : blk[row * 8 + col];
         if (bk == 0 || bk == 1 || bk == 3 || bk == 4) val = -val;
       } else if (bk == 2) {
         val = row == col ? 1.0 : 0.0;

@@ -16,18 +16,19 @@
 //     delta^(s) (Xi~ term, t-1 and t+1) for the TT steps: contiguous runs
 //     in the component-plane layout;
 //   * the Omega~ / Xi~ node blocks of the pair-row's two nodes.
-// Per pair-row i, with the factor blocks pre-multiplied by the inverted
-// pivots at setup (M1 = L0^-1 L1, M2 = L0^-1 L2, N1 = L0^-T L1_{i+1}',
-// N2 = L0^-T L2_{i+2}'):
-//   forward:  y_i = L0_i^-1 tau_i - M2_i y_{i-2} - M1_i y_{i-1}
-//   backward: x_i = L0_i^-T y_i - N2_i x_{i+2} - N1_i x_{i+1}
+// Per pair-row i, with the block Cholesky factor split at setup into a unit
+// block factor F and the pivots D (Phi_bar = F D F'; N1_i = F1_{i+1}',
+// N2_i = F2_{i+2}'):
+//   forward:  y_i = tau_i - F2_i y_{i-2} - F1_i y_{i-1}
+//   backward: x_i = D_i^-1 y_i - N2_i x_{i+2} - N1_i x_{i+1}
 // Each lane computes one row of every block product, from row-major blocks,
-// so a lane's operands are contiguous in shared memory.  The three products
-// are independent: only the last one waits for the previous pair-row's
-// result, which keeps the dependent chain of a step at 2n multiply-adds.
-// The group exchanges its 2n values of tau (or y) and of the result through
-// shared memory.  y is kept in theta_out between the two passes.  At t = 0,
-// Phi_bar = Q^-1 node by node, so theta = Q tau.
+// so a lane's operands are contiguous in shared memory.  Only the last
+// product of a step waits for the previous pair-row's result, which keeps
+// the dependent chain of a step at 2n multiply-adds.  The forward step
+// starts from the lane's own entry of tau; the backward step needs all 2n
+// values of y, and the group exchanges them, and each step's result,
+// through shared memory.  y is kept in theta_out between the two passes.
+// At t = 0, Phi_bar = Q^-1 node by node, so theta = Q tau.
 #pragma once
 
 #include <string.h>
@@ -137,7 +138,7 @@ struct SweepSmem {
   VT fac[NB][2][3 * Geo::BS];         // [buffer][class][3 blocks]
   VT halo[NB][Geo::NH][Geo::HW][NS];  // [buffer][h][t window][k]
   VT blk[NB][2][10][NS * NS];         // [buffer][jj][block][n x n]
-  VT xw[Geo::TT][Geo::G2];            // per group: right-hand side (tau or y) of the current step
+  VT xw[Geo::TT][Geo::G2];            // per group: y of the current backward step
   VT xy[Geo::TT][Geo::G2];            // per group: result (y or x) of the current step
   double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]; backward: r, y
   VT ys[NB][2][NS][Geo::TT];          // backward: forward result y of the pair-row
@@ -284,9 +285,9 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
 
   // ---- staging of the forward step for pair-row i into buffer b
   auto stage_forward = [&](int i, int b) {
-    // M2, M1, L0^-1 (record blocks 3..5) of pair-row i, per class
-    for (int e = tid * CH; e < ncls * 3 * BS; e += THR * CH) {
-      const int c = e / (3 * BS), off = e % (3 * BS);
+    // F2, F1 (record blocks 3..4) of pair-row i, per class
+    for (int e = tid * CH; e < ncls * 2 * BS; e += THR * CH) {
+      const int c = e / (2 * BS), off = e % (2 * BS);
       cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + 3 * BS + off);
     }
     if (t0 == 0) {
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
     }
   };
 
-  // ---- staging of the backward step for pair-row i: N2, N1 and L0^-T of
+  // ---- staging of the backward step for pair-row i: N2, N1 and D^-1 of
   // pair-row i (record blocks 0..2), the forward result y_i of the tile
   // (kept in theta_out between the passes; written by this CTA before the
   // barrier that ends the forward pass), and in the mu sweep r (and y of
@@ -451,18 +452,11 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       }
       if (node_ok) a.theta_out[kP + off] = out;
     } else {
-      // y_i = L0^-1 tau_i - M2 y_{i-2} - M1 y_{i-1}, one chain of
-      // multiply-adds (the FP64 pipe's issue rate, not its latency, bounds
-      // the sweep, so no partial sums are split off)
-      const VT* rec = sm.fac[b][my_slot];  // [M2][M1][L0^-1], row-major
-      if (lane_ok) sm.xw[grp][al] = tau;
-      __syncwarp(gmask);
-      VT tall[G2], row0[G2];
-      lds_run<VT, G2>(&sm.xw[grp][0], tall);
-      lds_run<VT, G2>(rec + 2 * BS + ac * G2, row0);
-      VT yv = VT(0);
-#pragma unroll
-      for (int bb = 0; bb < G2; ++bb) yv += row0[bb] * tall[bb];
+      // y_i = tau_i - F2 y_{i-2} - F1 y_{i-1}, one chain of multiply-adds
+      // (the FP64 pipe's issue rate, not its latency, bounds the sweep, so
+      // no partial sums are split off)
+      const VT* rec = sm.fac[b][my_slot];  // [F2][F1], row-major
+      VT yv = tau;
       if (i >= 2) {
         VT row[G2];
         lds_run<VT, G2>(rec + ac * G2, row);
@@ -517,8 +511,8 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       }
     }
     if (t >= 1) {
-      // x_i = L0^-T y_i - N2 x_{i+2} - N1 x_{i+1}
-      const VT* rec = sm.fac[b][my_slot];  // [N2][N1][L0^-T], row-major
+      // x_i = D^-1 y_i - N2 x_{i+2} - N1 x_{i+1}
+      const VT* rec = sm.fac[b][my_slot];  // [N2][N1][D^-1], row-major
       if (lane_ok) sm.xw[grp][al] = yown;
       __syncwarp(gmask);
       VT yall[G2], row0[G2];
