@@ -202,67 +202,132 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   constexpr int CH = 16 / sizeof(VT);  // elements per 16-byte copy
   double acc0 = 0.0, acc1 = 0.0;
 
-  // ---- staging descriptors.  Element e of every staged array maps to a
-  // fixed shared-memory slot and to a global offset that advances by one
-  // grid row (N nodes) per pair-row, so each thread computes its share of
-  // the copies once: for halo elements an int offset within the plane (for
-  // pair-row 0, negative for the row above) and a packed word
-  //   bit 0 in range, bits 1-3 h, bits 4-5 di+1, bits 6-9 k, bits 10.. shared slot.
+  // ---- staging descriptors.  Every staged array is a fixed set of
+  // elements per thread ("slots"): slot sl of thread tid is element
+  // e = tid + sl * THR (16-byte chunk e for the factor and node-block runs).
+  // An element's shared-memory place is fixed and its global address
+  // advances by one grid row (N nodes) per pair-row, so each thread keeps
+  // one pointer per slot, set for pair-row 0, and a step adds the row
+  // offset.  In-range flags are bit masks over the slots; for the halo the
+  // row above / below exists or not with the pair-row, which two more masks
+  // (slots with di < 0, di > 0) select.
+  const long long row_stride = (long long)g.N * Tp;
   const unsigned long long packed = XI ? kXiPacked : kOmPacked;
   constexpr int HALO_N = HALO ? Geo::NH * NS * HW : 0;
   constexpr int HSL = (HALO_N + THR - 1) / THR > 0 ? (HALO_N + THR - 1) / THR : 1;
-  int h_off[HSL];
-  unsigned h_meta[HSL];
+  const VT* h_ptr[HSL];
+  unsigned h_ok = 0u, h_up = 0u, h_dn = 0u;
+  if constexpr (HALO) {
+    const VT* vec = XI ? a.delta_s : a.theta_in;
 #pragma unroll
-  for (int sl = 0; sl < HSL; ++sl) {
-    const int e = tid + sl * THR;
-    // component fastest, so that consecutive threads fill consecutive words
-    // of the [h][w][k] staging array (the shared slot is e itself)
-    const int h = e / (NS * HW), w = (e / NS) % HW, kk = e % NS;
-    const int tt = t0 - 1 + w;
-    const unsigned code = (unsigned)((packed >> (5 * (h & 7))) & 31ull);
-    const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
-    const bool ok = e < HALO_N && tt >= 0 && tt <= g.T && jn >= 0 && jn < g.N;
-    h_off[sl] = (di * g.N + jn) * Tp + tt;
-    h_meta[sl] = (ok ? 1u : 0u) | ((unsigned)(h & 7) << 1) | ((unsigned)(di + 1) << 4) | ((unsigned)kk << 6) |
-                 ((unsigned)(e < HALO_N ? e : 0) << 10);
+    for (int sl = 0; sl < HSL; ++sl) {
+      // component fastest, so that consecutive threads fill consecutive
+      // words of the [h][w][k] staging array
+      const int e = tid + sl * THR;
+      const int h = e / (NS * HW), w = (e / NS) % HW, kk = e % NS;
+      const int tt = t0 - 1 + w;
+      const unsigned code = (unsigned)((packed >> (5 * (h & 7))) & 31ull);
+      const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
+      const bool ok = e < HALO_N && tt >= 0 && tt <= g.T && jn >= 0 && jn < g.N;
+      // pair-row 0's address; at di = -1 it lies one grid row below the
+      // plane's start and is used only from pair-row 1 on
+      h_ptr[sl] = vec + (ok ? kk * g.Ps + (long long)(di * g.N + jn) * Tp + tt : 0);
+      if (ok) h_ok |= 1u << sl;
+      if (di < 0) h_up |= 1u << sl;
+      if (di > 0) h_dn |= 1u << sl;
+    }
+  } else {
+    h_ptr[0] = nullptr;
   }
   // node blocks: runs of 5 n x n blocks per node (Omega~: Om of both nodes;
   // Xi~: AQ and QAt of both nodes), 16-byte chunks where a run is a multiple
-  // of 16 bytes; word: bit 0 in range, bits 1-2 run, bits 3.. shared slot
+  // of 16 bytes
   constexpr int RUN = 5 * NS * NS;
   constexpr int CB = (RUN * (int)sizeof(VT)) % 16 == 0 ? 16 / (int)sizeof(VT) : 1;
   constexpr int NRUN = XI ? 4 : 2;
   constexpr int BLK_N = HALO ? NRUN * (RUN / CB) : 0;
   constexpr int BSL = (BLK_N + THR - 1) / THR > 0 ? (BLK_N + THR - 1) / THR : 1;
-  int b_off[BSL];
-  unsigned b_meta[BSL];
+  const VT* b_ptr[BSL];
+  int b_sm[BSL];
+  unsigned b_ok = 0u;
 #pragma unroll
   for (int sl = 0; sl < BSL; ++sl) {
     const int c = tid + sl * THR;
     const int run = c / (RUN / CB), within = (c % (RUN / CB)) * CB;
     const int cjj = run & 1;
-    const bool ok = c < BLK_N && (cjj == 0 || two_cols);
-    b_off[sl] = (j0 + cjj) * RUN + within;
-    b_meta[sl] = (ok ? 1u : 0u) | ((unsigned)(run & 3) << 1) |
-                 ((unsigned)((cjj * 10 + (run >= 2 ? 5 : 0)) * NS * NS + within) << 3);
+    const bool ok = HALO && c < BLK_N && (cjj == 0 || two_cols);
+    const VT* arr = XI ? (run >= 2 ? pd.QAt : pd.AQ) : pd.Om;
+    b_ptr[sl] = ok ? arr + (size_t)(j0 + cjj) * RUN + within : nullptr;
+    b_sm[sl] = (cjj * 10 + (run >= 2 ? 5 : 0)) * NS * NS + within;
+    if (ok) b_ok |= 1u << sl;
   }
   // the pair-row's own entries for the tile (double): r, y, d, delta in the
-  // update sweep, else the source; word: bit 0 in range, bits 1-2 array,
-  // bits 3-6 k, bits 7.. shared slot
+  // update sweep, else the source; element e = ((vv * 2 + jj) * NS + k) * TT + t
   constexpr int NV = UPDATE ? 4 : 1;
   constexpr int SRC_N = NV * 2 * NS * TT;
   constexpr int SSL = (SRC_N + THR - 1) / THR;
-  int s_off[SSL];
-  unsigned s_meta[SSL];
+  const double* s_ptr[SSL];
+  unsigned s_ok = 0u;
 #pragma unroll
   for (int sl = 0; sl < SSL; ++sl) {
     const int e = tid + sl * THR;
     const int vv = e / (2 * NS * TT), cjj = (e / (NS * TT)) % 2, kk = (e / TT) % NS, gg = e % TT;
     const int tt = t0 + gg;
     const bool ok = e < SRC_N && tt <= g.T && (cjj == 0 || two_cols);
-    s_off[sl] = (j0 + cjj) * Tp + tt;
-    s_meta[sl] = (ok ? 1u : 0u) | ((unsigned)(vv & 3) << 1) | ((unsigned)kk << 3) | ((unsigned)(e % (NV * 2 * NS * TT)) << 7);
+    const double* base = UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src;
+    s_ptr[sl] = ok ? base + kk * g.Ps + (long long)(j0 + cjj) * Tp + tt : nullptr;
+    if (ok) s_ok |= 1u << sl;
+  }
+  // factor blocks, 16-byte chunks: forward F2, F1 (record blocks 3..4),
+  // backward N2, N1, D^-1 (blocks 0..2), per class present in the tile
+  constexpr int FSL = (2 * 2 * BS + THR * CH - 1) / (THR * CH);
+  constexpr int FSLB = (2 * 3 * BS + THR * CH - 1) / (THR * CH);
+  const VT* f_ptr[FSL];
+  int f_sm[FSL];
+  unsigned f_ok = 0u;
+#pragma unroll
+  for (int sl = 0; sl < FSL; ++sl) {
+    const int e = (tid + sl * THR) * CH;
+    const int c = e / (2 * BS), off = e % (2 * BS);
+    f_ptr[sl] = fac_pair + (size_t)c * pd.fac_vc + 3 * BS + off;
+    f_sm[sl] = c * 3 * BS + off;
+    if (e < ncls * 2 * BS) f_ok |= 1u << sl;
+  }
+  const VT* fb_ptr[FSLB];
+  unsigned fb_ok = 0u;
+#pragma unroll
+  for (int sl = 0; sl < FSLB; ++sl) {
+    const int e = (tid + sl * THR) * CH;  // also the shared-memory place
+    fb_ptr[sl] = fac_pair + (size_t)(e / (3 * BS)) * pd.fac_vc + e % (3 * BS);
+    if (e < ncls * 3 * BS) fb_ok |= 1u << sl;
+  }
+  // backward pass: the forward result y_i of the tile (kept in theta_out
+  // between the passes; written by this CTA before the barrier that ends the
+  // forward pass), and in the mu sweep r (and y of Algorithm 1 for the
+  // flexible ratio); element e = ((vv * 2 + jj) * NS + k) * TT + t, vv = 0
+  // for y_i (VT), 1.. for r, y (double)
+  constexpr int NVB = MU ? (FLEX ? 3 : 2) : 1;
+  constexpr int BN = NVB * 2 * NS * TT;
+  constexpr int BSLB = (BN + THR - 1) / THR;
+  const char* bs_ptr[BSLB];
+  int bs_sm[BSLB];
+  unsigned bs_ok = 0u, bs_y = 0u;
+#pragma unroll
+  for (int sl = 0; sl < BSLB; ++sl) {
+    const int e = tid + sl * THR;
+    const int vv = e / (2 * NS * TT), w = e % (2 * NS * TT), cjj = w / (NS * TT), gg = e % TT;
+    const int tt = t0 + gg;
+    const bool ok = e < BN && tt <= g.T && (cjj == 0 || two_cols);
+    const long long go = ((e / TT) % NS) * g.Ps + (long long)(j0 + cjj) * Tp + tt;
+    if (vv == 0) {
+      bs_ptr[sl] = ok ? reinterpret_cast<const char*>(a.theta_out + go) : nullptr;
+      bs_sm[sl] = w;
+      bs_y |= 1u << sl;
+    } else {
+      bs_ptr[sl] = ok ? reinterpret_cast<const char*>((vv == 1 ? a.r : a.y) + go) : nullptr;
+      bs_sm[sl] = (vv - 1) * 2 * NS * TT + w;
+    }
+    if (ok) bs_ok |= 1u << sl;
   }
   // staged neighbours inside the grid, by pair-row: the column test is fixed
   // for the CTA, the row test depends on whether the row above / below exists
@@ -281,15 +346,16 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
     if (i + 1 >= g.K) m &= ~below;
     return m;
   };
-  const long long row_stride = (long long)g.N * Tp;
 
-  // ---- staging of the forward step for pair-row i into buffer b
+  // ---- staging of the forward step for pair-row i into buffer b: F2, F1
+  // of pair-row i per class, Q of its nodes (tiles holding t = 0), its own
+  // entries, the neighbours' halo and the node blocks
   auto stage_forward = [&](int i, int b) {
-    // F2, F1 (record blocks 3..4) of pair-row i, per class
-    for (int e = tid * CH; e < ncls * 2 * BS; e += THR * CH) {
-      const int c = e / (2 * BS), off = e % (2 * BS);
-      cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + 3 * BS + off);
-    }
+    const long long rb = (long long)i * row_stride;
+    const long long fo = (long long)i * pd.fac_rec;
+#pragma unroll
+    for (int sl = 0; sl < FSL; ++sl)
+      if ((f_ok >> sl) & 1u) cp_async_16(&sm.fac[b][0][0] + f_sm[sl], f_ptr[sl] + fo);
     if (t0 == 0) {
       // Q of the pair-row's nodes, for theta = Q tau at t = 0
       for (int e = tid; e < 2 * NS * NS; e += THR) {
@@ -298,56 +364,39 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
         cp_async_elem(&sm.qb[b][cjj][w], pd.Qm + (size_t)(i * g.N + j0 + cjj) * NS * NS + w);
       }
     }
-    const long long rb = (long long)i * row_stride;
 #pragma unroll
-    for (int sl = 0; sl < SSL; ++sl) {
-      const unsigned m = s_meta[sl];
-      if (!(m & 1u)) continue;
-      const int vv = (m >> 1) & 3;
-      const double* base = UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src;
-      cp_async_8(&sm.src[b][0][0][0][0] + (m >> 7), base + ((m >> 3) & 15) * g.Ps + rb + s_off[sl]);
-    }
-    if (HALO) {
-      const VT* vec = (XI ? a.delta_s : a.theta_in) + rb;
+    for (int sl = 0; sl < SSL; ++sl)
+      if ((s_ok >> sl) & 1u) cp_async_8(&sm.src[b][0][0][0][0] + tid + sl * THR, s_ptr[sl] + rb);
+    if constexpr (HALO) {
+      const unsigned hv = h_ok & (i == 0 ? ~h_up : ~0u) & (i + 1 >= g.K ? ~h_dn : ~0u);
 #pragma unroll
-      for (int sl = 0; sl < HSL; ++sl) {
-        const unsigned m = h_meta[sl];
-        const int ii = i + (int)((m >> 4) & 3u) - 1;
-        if (!(m & 1u) || ii < 0 || ii >= g.K) continue;
-        cp_async_elem(&sm.halo[b][0][0][0] + (m >> 10), vec + ((m >> 6) & 15) * g.Ps + h_off[sl]);
-      }
+      for (int sl = 0; sl < HSL; ++sl)
+        if ((hv >> sl) & 1u) cp_async_elem(&sm.halo[b][0][0][0] + tid + sl * THR, h_ptr[sl] + rb);
       const long long bb = (long long)i * g.N * RUN;
 #pragma unroll
       for (int sl = 0; sl < BSL; ++sl) {
-        const unsigned m = b_meta[sl];
-        if (!(m & 1u)) continue;
-        const int run = (m >> 1) & 3;
-        const VT* arr = XI ? (run >= 2 ? pd.QAt : pd.AQ) : pd.Om;
-        if constexpr (CB > 1) cp_async_16(&sm.blk[b][0][0][0] + (m >> 3), arr + bb + b_off[sl]);
-        else cp_async_elem(&sm.blk[b][0][0][0] + (m >> 3), arr + bb + b_off[sl]);
+        if (!((b_ok >> sl) & 1u)) continue;
+        if constexpr (CB > 1) cp_async_16(&sm.blk[b][0][0][0] + b_sm[sl], b_ptr[sl] + bb);
+        else cp_async_elem(&sm.blk[b][0][0][0] + b_sm[sl], b_ptr[sl] + bb);
       }
     }
   };
 
   // ---- staging of the backward step for pair-row i: N2, N1 and D^-1 of
-  // pair-row i (record blocks 0..2), the forward result y_i of the tile
-  // (kept in theta_out between the passes; written by this CTA before the
-  // barrier that ends the forward pass), and in the mu sweep r (and y of
-  // Algorithm 1 for the flexible ratio) of the tile
-  constexpr int NVB = MU ? (FLEX ? 3 : 2) : 1;
+  // pair-row i, y_i of the tile and, in the mu sweep, r (and y)
   auto stage_backward = [&](int i, int b) {
-    for (int e = tid * CH; e < ncls * 3 * BS; e += THR * CH) {
-      const int c = e / (3 * BS), off = e % (3 * BS);
-      cp_async_16(&sm.fac[b][c][off], fac_pair + (size_t)c * pd.fac_vc + (size_t)i * pd.fac_rec + off);
-    }
+    const long long fo = (long long)i * pd.fac_rec;
+#pragma unroll
+    for (int sl = 0; sl < FSLB; ++sl)
+      if ((fb_ok >> sl) & 1u) cp_async_16(&sm.fac[b][0][0] + (tid + sl * THR) * CH, fb_ptr[sl] + fo);
     const long long rb = (long long)i * row_stride;
-    for (int e = tid; e < NVB * 2 * NS * TT; e += THR) {
-      const int vv = e / (2 * NS * TT), cjj = (e / (NS * TT)) % 2, kk = (e / TT) % NS, gg = e % TT;
-      const int tt = t0 + gg;
-      if (tt > g.T || (cjj == 1 && !two_cols)) continue;
-      const long long go = kk * g.Ps + rb + (long long)(j0 + cjj) * Tp + tt;
-      if (vv == 0) cp_async_elem(&sm.ys[b][cjj][kk][gg], (const VT*)a.theta_out + go);
-      else cp_async_8(&sm.src[b][vv - 1][cjj][kk][gg], (vv == 1 ? a.r : a.y) + go);
+#pragma unroll
+    for (int sl = 0; sl < BSLB; ++sl) {
+      if (!((bs_ok >> sl) & 1u)) continue;
+      if ((bs_y >> sl) & 1u)
+        cp_async_elem(&sm.ys[b][0][0][0] + bs_sm[sl], reinterpret_cast<const VT*>(bs_ptr[sl]) + rb);
+      else
+        cp_async_8(&sm.src[b][0][0][0][0] + bs_sm[sl], reinterpret_cast<const double*>(bs_ptr[sl]) + rb);
     }
   };
 
