@@ -65,6 +65,9 @@ def parse_args():
                          "K = N = 128, T = 100 family, then time held-out solves from its guess and from zero")
     ap.add_argument("--ws-steps", type=int, default=1500, help="training steps of the warm-start network")
     ap.add_argument("--ws-eval", type=int, default=50, help="held-out instances (seeds 100000+) evaluated")
+    ap.add_argument("--ws-buffer", type=int, default=2048,
+                    help="training pairs kept on the device; with more --warmstart instances than this the "
+                         "network trains online (pairs generated group by group into a ring buffer)")
     ap.add_argument("--ws-group", type=int, default=32,
                     help="training pairs per multi-right-hand-side solve (seeds sharing one coupling value); "
                          "1 = one mixed-precision solve per pair")
@@ -606,19 +609,32 @@ def run_warmstart(args, dist):
     torch.cuda.set_device(dev)
     fam = synth.warmstart_family()
     ws = warmstart.WarmStart(fam, channels=64, layers=6, batch=8, seed=0, device=str(dev))
-    if args.ws_group > 1:
-        gen_s = ws.generate_grouped(range(1000, 1000 + args.warmstart), tol=1e-6, group=args.ws_group)
+    seeds = range(1000, 1000 + args.warmstart)
+    online = args.warmstart > args.ws_buffer
+    if online:
+        # output scale from the first group; then pairs are generated group
+        # by group while the network trains
+        ws.generate_grouped(seeds[:args.ws_group], tol=1e-6, group=args.ws_group)
+    elif args.ws_group > 1:
+        gen_s = ws.generate_grouped(seeds, tol=1e-6, group=args.ws_group)
     else:
-        gen_s = ws.generate(range(1000, 1000 + args.warmstart), tol=1e-6, precision=1)
+        gen_s = ws.generate(seeds, tol=1e-6, precision=1)
     sigma = float(ws.targets.std())
     ws.net.close()
     ws.net = lq2d.WarmStartNet(fam.K, fam.N, fam.T, fam.n, 64, 6, 8, sigma)
     ws.net.set_params(synth.warmstart_init(ws.net.layer_sizes(), 0, 0.1))
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    losses = ws.fit(args.ws_steps, lr=1e-3, lr_final=5e-5)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    if online:
+        groups = (args.warmstart + args.ws_group - 1) // args.ws_group
+        per_group = max(1, -(-args.ws_steps // groups))
+        losses, gen_s, train_s, _ = ws.fit_online(seeds, per_group, tol=1e-6, group=args.ws_group,
+                                                  buffer=args.ws_buffer, lr=1e-3, lr_final=5e-5)
+        args.ws_steps = per_group * groups
+    else:
+        t0 = time.perf_counter()
+        losses = ws.fit(args.ws_steps, lr=1e-3, lr_final=5e-5)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
     fl = conv_flops_per_sample(ws.net.layer_sizes(), fam.K, fam.N)
     train_tflops = 3.0 * fl * 8 * args.ws_steps / train_s / 1e12
     # warm-up of every path, then the held-out instances: zero and learned
@@ -662,7 +678,9 @@ def run_warmstart(args, dist):
         "config": {"workload": "warmstart K = N = 128, n = 4, m = 2, T = 100, coupling 0.02..0.2, x0 ~ N(0, 1)",
                    "train_instances": args.warmstart, "train_steps": args.ws_steps, "batch": 8,
                    "train_generation": ("multi-right-hand-side solves at tol 1e-6, %d seeds per coupling value"
-                                        % args.ws_group if args.ws_group > 1 else "mixed-precision solves at tol 1e-6"),
+                                        % args.ws_group if args.ws_group > 1 else "mixed-precision solves at tol 1e-6")
+                                       + ("; online: a ring buffer of %d pairs on the device, training steps "
+                                          "after each group" % args.ws_buffer if online else ""),
                    "net": "6 x conv3x3, 64 channels, 404 outputs", "eval_instances": args.ws_eval, "tol": args.tol},
         "zero_start_ms": zero_ms, "speedup_vs_zero_start": zero_ms / warm_ms,
         "iterations_zero": float(np.mean(zero_it)), "iterations_warm": float(np.mean(warm_it)),

@@ -101,6 +101,68 @@ class WarmStart:
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
+    def fit_online(self, seeds, steps_per_group: int, tol: float = 1e-6, S: int = 2, L: int = 2,
+                   group: int = 32, buffer: int = 2048, lr: float = 1e-3, lr_final: float = 1e-4,
+                   seed: int = 0):
+        """Training without storing every target (20k FP64 solutions of the
+        128 x 128 x 100 family take about 1 TB): consecutive seeds are solved
+        `group` at a time (the rule of generate_grouped), their pairs go into
+        a ring buffer of `buffer` pairs on the device, and after each group
+        `steps_per_group` Adam steps sample minibatches from the pairs in the
+        buffer.  The learning rate decays geometrically from lr to lr_final
+        over all steps.  Returns (losses, generation seconds, training
+        seconds, pairs generated)."""
+        torch = _torch()
+        f = self.family
+        seeds = list(seeds)
+        if buffer % group != 0:
+            raise ValueError("buffer must be a multiple of group")
+        cap = min(buffer, len(seeds) + (-len(seeds)) % group)
+        self.x0 = torch.empty((cap, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.targets = torch.empty((cap, f.T + 1, f.K * f.N, f.n), dtype=torch.float64, device=self.dev)
+        self.couplings = np.zeros(cap)
+        its = []
+        groups = (len(seeds) + group - 1) // group
+        total = groups * steps_per_group
+        rng = np.random.default_rng(seed)
+        b = self.batch
+        xb = torch.empty((b,) + tuple(self.x0.shape[1:]), dtype=torch.float64, device=self.dev)
+        tb = torch.empty((b,) + tuple(self.targets.shape[1:]), dtype=torch.float64, device=self.dev)
+        losses = []
+        gen_s = train_s = 0.0
+        step = 0
+        for gi in range(groups):
+            chunk = seeds[gi * group:(gi + 1) * group]
+            slot = (gi * group) % cap
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c = f.instance_params(chunk[0])[0]
+            for k, sd in enumerate(chunk):
+                self.x0[slot + k].copy_(torch.from_numpy(f.instance_params(sd)[1]))
+                self.couplings[slot + k] = c
+            prob = self._problem_for(f.grid(c, f.instance_params(chunk[0])[1]))
+            out = prob.solve_multi_device(len(chunk), self.x0[slot:slot + len(chunk)], tol, S, L, 100000,
+                                          costate=self.targets[slot:slot + len(chunk)])
+            its.extend(out["iterations"])
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            gen_s += t1 - t0
+            avail = min(cap, gi * group + len(chunk))
+            for _ in range(steps_per_group):
+                idx = rng.choice(avail, size=min(b, avail), replace=False)
+                if len(idx) < b:
+                    idx = np.resize(idx, b)
+                ii = torch.from_numpy(idx).to(self.dev)
+                torch.index_select(self.x0, 0, ii, out=xb)
+                torch.index_select(self.targets, 0, ii, out=tb)
+                rate = lr * (lr_final / lr) ** (step / max(1, total - 1))
+                losses.append(self.net.train_step_device(b, xb, self.couplings[idx], tb, rate))
+                step += 1
+            torch.cuda.synchronize()
+            train_s += time.perf_counter() - t1
+        self.iterations = np.array(its, dtype=np.int64)
+        return np.array(losses), gen_s, train_s, len(seeds)
+
     # -- training --------------------------------------------------------
     def fit(self, steps: int, lr: float = 1e-3, lr_final: float = 1e-4, seed: int = 0, log_every: int = 0):
         """Adam steps on random minibatches of the generated pairs, with the

@@ -187,3 +187,29 @@ def test_grouped_generation_matches_the_oracle(dev):
         assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref)
     assert np.all(ws.iterations > 0)
     ws.close()
+
+
+def test_online_training_keeps_a_ring_buffer_of_solved_pairs(dev):
+    """fit_online: five groups of 8 seeds through a buffer of 16 pairs, three
+    Adam steps after each group; the buffer ends holding the last two
+    groups, each target that instance's costate."""
+    from paper_2304_04980_gb300 import warmstart
+    fam = synth.warmstart_family(6, 6, 7, 4, 2, seed=13)
+    ws = warmstart.WarmStart(fam, channels=8, layers=2, batch=4, seed=0)
+    seeds = list(range(3000, 3040))
+    losses, gen_s, train_s, count = ws.fit_online(seeds, 3, tol=1e-10, group=8, buffer=16, lr=1e-3,
+                                                  lr_final=1e-4)
+    assert count == 40 and len(losses) == 15 and np.all(np.isfinite(losses))
+    assert gen_s > 0 and train_s > 0 and len(ws.iterations) == 40
+    # slot 0..7: group 4 (seeds 3032..3039), slot 8..15: group 3 (3024..3031)
+    for slot, sd, first in ((0, 3032, 3032), (7, 3039, 3032), (8, 3024, 3024), (15, 3031, 3024)):
+        c = fam.instance_params(first)[0]
+        x0 = fam.instance_params(sd)[1]
+        assert ws.couplings[slot] == c
+        assert np.array_equal(ws.x0[slot].cpu().numpy(), x0)
+        g = fam.grid(c, x0)
+        ref = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())).solve(1e-12).delta
+        assert np.linalg.norm(ws.targets[slot].cpu().numpy() - ref) <= 1e-7 * np.linalg.norm(ref)
+    with pytest.raises(ValueError):
+        ws.fit_online(seeds, 1, group=8, buffer=12)
+    ws.close()
