@@ -72,6 +72,22 @@ class WarmStart:
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
+    def _solve_group(self, chunk, slot: int, tol: float, S: int, L: int):
+        """Solves the seeds of `chunk` as one multi-right-hand-side problem
+        with the coupling of chunk[0] (each seed keeps its own x0) and writes
+        x0, c and the costates to pair slots slot, slot + 1, ...; returns the
+        iteration count of each pair."""
+        torch = _torch()
+        f = self.family
+        c, x0_first = f.instance_params(chunk[0])
+        for k, sd in enumerate(chunk):
+            self.x0[slot + k].copy_(torch.from_numpy(f.instance_params(sd)[1]))
+            self.couplings[slot + k] = c
+        prob = self._problem_for(f.grid(c, x0_first))
+        out = prob.solve_multi_device(len(chunk), self.x0[slot:slot + len(chunk)], tol, S, L, 100000,
+                                      costate=self.targets[slot:slot + len(chunk)])
+        return out["iterations"]
+
     def generate_grouped(self, seeds, tol: float = 1e-6, S: int = 2, L: int = 2, group: int = 32):
         """As generate, 32 instances per solve: consecutive seeds form groups
         of `group` that share the coupling drawn by the group's first seed
@@ -89,15 +105,8 @@ class WarmStart:
         self.iterations = np.empty(count, dtype=np.int64)
         t0 = time.perf_counter()
         for start in range(0, count, group):
-            idx = list(range(start, min(start + group, count)))
-            c = f.instance_params(seeds[idx[0]])[0]
-            for k in idx:
-                self.x0[k].copy_(torch.from_numpy(f.instance_params(seeds[k])[1]))
-                self.couplings[k] = c
-            prob = self._problem_for(f.grid(c, f.instance_params(seeds[idx[0]])[1]))
-            out = prob.solve_multi_device(len(idx), self.x0[idx[0]:idx[-1] + 1], tol, S, L, 100000,
-                                          costate=self.targets[idx[0]:idx[-1] + 1])
-            self.iterations[idx[0]:idx[-1] + 1] = out["iterations"]
+            chunk = seeds[start:start + group]
+            self.iterations[start:start + len(chunk)] = self._solve_group(chunk, start, tol, S, L)
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
@@ -136,14 +145,7 @@ class WarmStart:
             slot = (gi * group) % cap
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            c = f.instance_params(chunk[0])[0]
-            for k, sd in enumerate(chunk):
-                self.x0[slot + k].copy_(torch.from_numpy(f.instance_params(sd)[1]))
-                self.couplings[slot + k] = c
-            prob = self._problem_for(f.grid(c, f.instance_params(chunk[0])[1]))
-            out = prob.solve_multi_device(len(chunk), self.x0[slot:slot + len(chunk)], tol, S, L, 100000,
-                                          costate=self.targets[slot:slot + len(chunk)])
-            its.extend(out["iterations"])
+            its.extend(self._solve_group(chunk, slot, tol, S, L))
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             gen_s += t1 - t0
@@ -152,11 +154,8 @@ class WarmStart:
                 idx = rng.choice(avail, size=min(b, avail), replace=False)
                 if len(idx) < b:
                     idx = np.resize(idx, b)
-                ii = torch.from_numpy(idx).to(self.dev)
-                torch.index_select(self.x0, 0, ii, out=xb)
-                torch.index_select(self.targets, 0, ii, out=tb)
                 rate = lr * (lr_final / lr) ** (step / max(1, total - 1))
-                losses.append(self.net.train_step_device(b, xb, self.couplings[idx], tb, rate))
+                losses.append(self._train_step(idx, xb, tb, rate))
                 step += 1
             torch.cuda.synchronize()
             train_s += time.perf_counter() - t1
@@ -164,6 +163,14 @@ class WarmStart:
         return np.array(losses), gen_s, train_s, len(seeds)
 
     # -- training --------------------------------------------------------
+    def _train_step(self, idx, xb, tb, rate: float) -> float:
+        """One Adam step on the stored pairs idx (gathered into xb, tb)."""
+        torch = _torch()
+        ii = torch.from_numpy(idx).to(self.dev)
+        torch.index_select(self.x0, 0, ii, out=xb)
+        torch.index_select(self.targets, 0, ii, out=tb)
+        return self.net.train_step_device(len(idx), xb, self.couplings[idx], tb, rate)
+
     def fit(self, steps: int, lr: float = 1e-3, lr_final: float = 1e-4, seed: int = 0, log_every: int = 0):
         """Adam steps on random minibatches of the generated pairs, with the
         learning rate decayed geometrically from lr to lr_final.  Returns the
@@ -177,11 +184,8 @@ class WarmStart:
         tb = torch.empty((b,) + tuple(self.targets.shape[1:]), dtype=torch.float64, device=self.dev)
         for s in range(steps):
             idx = rng.choice(count, size=b, replace=False)
-            ii = torch.from_numpy(idx).to(self.dev)
-            torch.index_select(self.x0, 0, ii, out=xb)
-            torch.index_select(self.targets, 0, ii, out=tb)
             rate = lr * (lr_final / lr) ** (s / max(1, steps - 1))
-            losses.append(self.net.train_step_device(b, xb, self.couplings[idx], tb, rate))
+            losses.append(self._train_step(idx, xb, tb, rate))
             if log_every and (s % log_every == 0 or s + 1 == steps):
                 print("step %d loss %.4e lr %.2e" % (s, losses[-1], rate), flush=True)
         return np.array(losses)
