@@ -146,8 +146,18 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        os.unlink(self.path)
+        return self.parse(lines)
+
+    @classmethod
+    def parse(cls, lines):
+        """Median SM clock, maximum clock and the throttle reasons seen in
+        nvidia-smi's CSV samples (the FIELDS columns, no header, no units);
+        None without a usable sample."""
         sm, mx, reasons = [], [], set()
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -156,10 +166,9 @@ class Clocks:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
-            for name, val in zip(self.NAMES, parts[5:9]):
+            for name, val in zip(cls.NAMES, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
-        os.unlink(self.path)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
