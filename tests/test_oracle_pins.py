@@ -395,3 +395,15 @@ def test_lanczos_estimates_match_dense_condition_numbers():
     pc = O.pcg(orc.Delta, orc.r_delta, orc.preconditioner(2, 2).apply, 1e-13, 10000)
     lo, hi = O.lanczos_extremes(pc.alphas, pc.betas)
     assert abs(hi / lo - evp[-1] / evp[0]) <= 0.02 * evp[-1] / evp[0]
+
+
+def test_pcgm_steps_grow_at_most_linearly_with_the_grid():
+    """Section V reports PCGM step counts that grow about linearly with K on
+    its second case study; on the diffusion grids (K = N, T = 10, n = 4) the
+    counts grow with K and no faster than K."""
+    its = []
+    for K in (4, 8, 16):
+        g = synth.diffusion_grid(K, K, 10, 4, 2, seed=1)
+        its.append(O.Oracle(as_problem(g)).solve(1e-10).iterations)
+    assert its[0] <= its[1] <= its[2]
+    assert its[1] <= 2 * its[0] and its[2] <= 2 * its[1]
