@@ -51,7 +51,9 @@ enum {
   LQ2D_ENOCONV = 3,     /* max_iter reached; outputs hold the last iterate */
   LQ2D_EBREAKDOWN = 4,  /* y'd <= 0 or a non-finite scalar inside Algorithm 1 */
   LQ2D_ECUDA = 5,       /* a CUDA call failed */
-  LQ2D_ENOMEM = 6,      /* device allocation failed */
+  LQ2D_ENOMEM = 6,      /* device allocation failed (the environment variable
+                           LQ2D_FAIL_ALLOC_AT=k makes a handle's k-th device
+                           allocation fail on the host, for tests of this path) */
   LQ2D_ETIMEOUT = 7     /* the device loop hit its hard iteration cap */
 };
 
@@ -267,11 +269,16 @@ int lq2d_autotune(lq2d_problem *h, int outer_S, int inner_L, int reps, int *thre
  *   every GPU that loads the library until the process exits); larger
  *   problems return LQ2D_EINVAL with the required size in the message.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current) and caches it; make
- *   that first call before any stream capture.  All calls share the array
- *   and it keeps the last call's contents; calls whose work overlaps on the
- *   GPU race on it.  Calls no cudaMalloc or cudaFree.  Returns after the
- *   work on `stream` is complete; LQ2D_ENOTPD if Q, Q_T or R is not SPD. */
+ *   (cudaGetSymbolAddress, with that device current) and caches it.  With
+ *   lazy module loading (the CUDA default) that first call also loads the
+ *   library's device code on the device, which reserves the array, so
+ *   make it during set-up, before a fixed-period loop and before any
+ *   stream capture.  All calls share the array and it keeps the last
+ *   call's contents; calls whose work overlaps on the GPU race on it.
+ *   Calls no cudaMalloc or cudaFree.  Every call is synchronous: it reads
+ *   a status word back on `stream` and returns after the work on `stream`
+ *   is complete.  d_in and d_out must not overlap (LQ2D_EINVAL).
+ *   LQ2D_ENOTPD if Q, Q_T or R is not SPD. */
 int lq2d_apply_delta_static(int K, int N, int T, int n, int m,
                             const double *d_A_self, const double *d_A_nbr, const double *d_B,
                             const double *d_Q, const double *d_R, const double *d_Q_T,

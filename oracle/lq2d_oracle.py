@@ -622,3 +622,100 @@ def delta_rows_matrix_free(P: Problem, rows: np.ndarray, vec: np.ndarray) -> np.
             val += Sblk[p, k] @ V[t, p * n:(p + 1) * n]
         out[o] = val
     return out
+
+
+# --------------------------------------------------------------------------
+# Slab-by-slab evaluation for grids too large to assemble (Section II)
+# --------------------------------------------------------------------------
+#
+# The stacked matrices of eq. (t_stacked_LQ_problem) have a fixed pattern of
+# per-slab blocks: A~ holds -I on its diagonal and A_hat in block (t, t-1);
+# B~ holds B_hat in block (t, t-1) for t = 1..T and nothing in block row 0;
+# Q~ = blkdiag(Q, ..., Q, Q_T) and R~ = blkdiag(R, ..., R).  The functions
+# below apply the definitions of Section II-B one time slab at a time with
+# these blocks, so the memory they need is a few slabs, not the assembled
+# (T+1)KNn-square Delta.  They evaluate the same products as schur_matrix
+# and recover, in the same order of factors.
+
+@dataclasses.dataclass
+class SlabBlocks:
+    Ahat: sp.csr_matrix     # A_hat (eq. h_stacked_LQ_problem)
+    AhatT: sp.csr_matrix    # A_hat'
+    Bhat: sp.csr_matrix     # B_hat = blkdiag(B_{i,j})
+    BhatT: sp.csr_matrix
+    Qinv: sp.csr_matrix     # Q^-1 (slabs t < T)
+    QTinv: sp.csr_matrix    # Q_T^-1 (slab T)
+    Rinv: sp.csr_matrix     # R^-1
+
+
+def slab_blocks(P: Problem) -> SlabBlocks:
+    Ahat = grid_dynamics_matrix(P)
+    Bhat = block_diag_sparse(P.B)
+    return SlabBlocks(Ahat, Ahat.T.tocsr(), Bhat, Bhat.T.tocsr(),
+                      block_diag_sparse(blockwise_inverse(P.Q)), block_diag_sparse(blockwise_inverse(P.Q_T)),
+                      block_diag_sparse(blockwise_inverse(P.R)))
+
+
+def rhs_slabs(P: Problem) -> np.ndarray:
+    """r_delta = -omega~ as [(T+1), K*N*n] (reading A1: omega~ = col(gamma,
+    omega_0, ..., omega_{T-1}))."""
+    r = np.zeros((P.T + 1, P.nodes * P.n))
+    r[0] = -P.x0.ravel()
+    if P.w is not None:
+        r[1:] = -P.w.reshape(P.T, -1)
+    return r
+
+
+def delta_apply_slabs(P: Problem, vec: np.ndarray, blocks: Optional[SlabBlocks] = None) -> np.ndarray:
+    """Delta vec = A~ (Q~^-1 (A~' vec)) + B~ (R~^-1 (B~' vec)) (below eq.
+    kkt_conditions), one time slab at a time:
+        (A~' vec)_t = -vec_t + A_hat' vec_{t+1}  (t < T),   -vec_T  (t = T)
+        z_t = Q_t^-1 (A~' vec)_t                 (Q_T^-1 at t = T)
+        (A~ z)_0 = -z_0,   (A~ z)_t = A_hat z_{t-1} - z_t
+        (B~' vec)_{t-1} = B_hat' vec_t,   (B~ R~^-1 B~' vec)_t = B_hat R^-1 B_hat' vec_t  (t >= 1).
+    vec and the result are [(T+1), K*N*n] (any shape of that size in)."""
+    b = blocks if blocks is not None else slab_blocks(P)
+    T = P.T
+    V = np.asarray(vec, dtype=np.float64).reshape(T + 1, P.nodes * P.n)
+    out = np.empty_like(V)
+    z_prev = None
+    for t in range(T + 1):
+        w = -V[t]
+        if t < T:
+            w = w + b.AhatT @ V[t + 1]
+        z = (b.QTinv if t == T else b.Qinv) @ w
+        y = -z
+        if t >= 1:
+            y = y + b.Ahat @ z_prev
+            y = y + b.Bhat @ (b.Rinv @ (b.BhatT @ V[t]))
+        out[t] = y
+        z_prev = z
+    return out
+
+
+def recover_slabs(P: Problem, delta: np.ndarray, blocks: Optional[SlabBlocks] = None):
+    """x = Q~^-1 A~' delta and u = R~^-1 B~' delta (Section II-B), slab by
+    slab: x_t = Q_t^-1 (-delta_t + A_hat' delta_{t+1}) (no second term at
+    t = T), u_t = R^-1 B_hat' delta_{t+1}.  Returns x [(T+1), K*N*n] and
+    u [T, K*N*m]."""
+    b = blocks if blocks is not None else slab_blocks(P)
+    T = P.T
+    D = np.asarray(delta, dtype=np.float64).reshape(T + 1, P.nodes * P.n)
+    x = np.empty_like(D)
+    u = np.empty((T, P.nodes * P.m))
+    for t in range(T + 1):
+        w = -D[t]
+        if t < T:
+            w = w + b.AhatT @ D[t + 1]
+            u[t] = b.Rinv @ (b.BhatT @ D[t + 1])
+        x[t] = (b.QTinv if t == T else b.Qinv) @ w
+    return x, u
+
+
+def true_residual_slabs(P: Problem, delta: np.ndarray, blocks: Optional[SlabBlocks] = None) -> float:
+    """||r_delta - Delta delta||_2 / ||r_delta||_2, the relative true residual
+    of the reduced system (reading A9), evaluated slab by slab."""
+    b = blocks if blocks is not None else slab_blocks(P)
+    r = rhs_slabs(P)
+    res = r - delta_apply_slabs(P, delta, b)
+    return float(np.linalg.norm(res) / np.linalg.norm(r))

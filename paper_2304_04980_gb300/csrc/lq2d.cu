@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -131,9 +132,22 @@ namespace {
 
 constexpr int kBatchSlot = 32;  // doubles per problem in the batch result array
 
+// Failure injection for the allocation path, on the host: with the
+// environment variable LQ2D_FAIL_ALLOC_AT=k (k >= 1), the k-th device
+// allocation of every handle reports cudaErrorMemoryAllocation without
+// calling cudaMalloc, so the LQ2D_ENOMEM path and the release of the
+// allocations made before it can be tested without exhausting a GPU.
+bool simulated_alloc_failure(const lq2d_problem* h) {
+  const char* v = std::getenv("LQ2D_FAIL_ALLOC_AT");
+  if (v == nullptr || *v == '\0') return false;
+  const long k = std::strtol(v, nullptr, 10);
+  return k >= 1 && (long)h->allocs.size() + 1 == k;
+}
+
 int dev_alloc(lq2d_problem* h, double** p, size_t count) {
   void* ptr = nullptr;
-  cudaError_t e = cudaMalloc(&ptr, count * sizeof(double) + 256);
+  cudaError_t e = simulated_alloc_failure(h) ? cudaErrorMemoryAllocation
+                                             : cudaMalloc(&ptr, count * sizeof(double) + 256);
   if (e != cudaSuccess) return fail(LQ2D_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   h->allocs.push_back(ptr);
   *p = static_cast<double*>(ptr);

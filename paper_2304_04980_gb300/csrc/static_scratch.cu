@@ -11,10 +11,13 @@
 //
 // The scratch array holds the per-node blocks Q^-1, Q_T^-1, B R^-1 B' and the
 // intermediate z = Q~^-1 A~' d.  Every GPU that loads the library holds it
-// until the process exits.  All calls share it and it keeps the last call's
-// contents; both parts are rewritten in full by every call, so nothing in it
-// has to start at zero.  Calls whose work overlaps on the GPU (different
-// streams, or different host threads on one device) race on it.
+// until the process exits; with lazy module loading (the CUDA default) the
+// module and its array are loaded on a device by the first call there, so
+// that call belongs in a caller's set-up, before its fixed-period loop.
+// All calls share the array and it keeps the last call's contents; both
+// parts are rewritten in full by every call, so nothing in it has to start
+// at zero.  Calls whose work overlaps on the GPU (different streams, or
+// different host threads on one device) race on it.
 #include <mutex>
 #include <string>
 
@@ -158,8 +161,13 @@ __global__ void static_y_kernel(int K, int N, int T, int n, const double* __rest
 int scratch_on_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     lq2d::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return LQ2D_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    lq2d::set_last_error("lq2d_apply_delta_static: device index " + std::to_string(dev) +
+                         " is beyond the " + std::to_string(kMaxDevices) + " devices the library tracks");
     return LQ2D_ECUDA;
   }
   std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -191,11 +199,20 @@ extern "C" int lq2d_apply_delta_static(int K, int N, int T, int n, int m, const 
     return LQ2D_EINVAL;
   }
   const long long NN = (long long)K * N;
-  const long long need = NN * (T + 1) * n + NN * 3LL * n * n + 1;  // z, node blocks, status word
+  const long long need = NN * (T + 1LL) * n + NN * 3LL * n * n + 1;  // z, node blocks, status word
   if (need > kStaticScratchDoubles) {
     lq2d::set_last_error("lq2d_apply_delta_static: problem needs " + std::to_string(need) +
                    " scratch doubles, more than the fixed " + std::to_string(kStaticScratchDoubles) +
                    " (require (T+1)*K*N*n + 3*K*N*n*n + 1 <= that)");
+    return LQ2D_EINVAL;
+  }
+  // the product reads d while it writes y (y is declared restrict in the
+  // kernels), so the two ranges must not overlap
+  const long long bytes = NN * (T + 1LL) * n * (long long)sizeof(double);
+  const char* in_b = static_cast<const char*>(d_in);
+  const char* out_b = static_cast<const char*>(d_out);
+  if (in_b < out_b + bytes && out_b < in_b + bytes) {
+    lq2d::set_last_error("lq2d_apply_delta_static: d_in and d_out overlap");
     return LQ2D_EINVAL;
   }
   double* scratch = nullptr;

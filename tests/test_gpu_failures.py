@@ -77,3 +77,28 @@ def test_iteration_cap_returns_enoconv_with_outputs(dev):
     assert res["statuses"][0] == lq2d.ENOCONV
     batch.close()
     prob.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 16, 24])
+def test_allocation_failure_returns_enomem_and_releases_memory(dev, k, monkeypatch):
+    """A device allocation that fails during creation (injected on the host
+    through LQ2D_FAIL_ALLOC_AT, no GPU memory exhausted) returns
+    LQ2D_ENOMEM, releases the allocations made before it, and leaves the
+    library usable."""
+    lq2d = lq()
+    g = synth.workload("grid64_T100")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    monkeypatch.setenv("LQ2D_FAIL_ALLOC_AT", str(k))
+    with pytest.raises(lq2d.LQ2DError) as e:
+        lq2d.Problem.from_grid(g)
+    assert e.value.code == lq2d.ENOMEM and "cudaMalloc" in str(e.value)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    # the allocations before the k-th hold over 100 MB at k = 24
+    assert abs(free1 - free0) <= 8 << 20
+    monkeypatch.delenv("LQ2D_FAIL_ALLOC_AT")
+    small = synth.random_grid(3, 3, 5, 2, 1, seed=3)
+    with lq2d.Problem.from_grid(small) as prob:
+        out = prob.solve(1e-10, 2, 2, 200)
+    assert out["status"] == 0

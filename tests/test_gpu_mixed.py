@@ -132,29 +132,3 @@ def test_mixed_full_size_bench_workload(dev, mode):
         out["x"][t + 1] - grid_sim.step(g.K, g.N, g.A_self, g.A_nbr, g.B, out["x"][t], out["u"][t])
         for t in range(g.T)]
     assert np.linalg.norm(np.array(res)) <= 1e-9 * np.linalg.norm(g.x0)
-
-
-def test_mixed_full_size_grid256_T200(dev):
-    """The K = N = 256, T = 200 workload (52.7 M unknowns), mixed precision:
-    the error against the FP64 GPU solution (itself checked against the
-    oracle at smaller sizes) and sampled rows of the true residual from the
-    oracle's row evaluation."""
-    g = synth.workload("grid256_T200")
-    prob = lq().Problem.from_grid(g)
-    plain = prob.solve(1e-8, 2, 2, 5000)
-    prob.set_precision(1)
-    out = prob.solve(1e-8, 2, 2, 5000)
-    assert plain["status"] == 0 and out["status"] == 0
-    assert out["rel_kkt"] <= 1e-8
-    assert rel_err(out["costate"], plain["costate"]) <= 1e-6
-    prob.set_precision(2)
-    out2 = prob.solve(1e-8, 2, 2, 5000)
-    assert out2["status"] == 0 and out2["rel_kkt"] <= 1e-8
-    assert rel_err(out2["costate"], plain["costate"]) <= 1e-6
-    P = O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())
-    rows = np.random.default_rng(11).choice(P.dim_x, 12, replace=False)
-    rd = np.zeros(len(rows))
-    first = rows < g.nodes * g.n
-    rd[first] = -g.x0.ravel()[rows[first]]
-    res = rd - O.delta_rows_matrix_free(P, rows, out["costate"].ravel())
-    assert np.abs(res).max() <= 1e-8 * np.linalg.norm(g.x0)

@@ -407,3 +407,77 @@ def test_pcgm_steps_grow_at_most_linearly_with_the_grid():
         its.append(O.Oracle(as_problem(g)).solve(1e-10).iterations)
     assert its[0] <= its[1] <= its[2]
     assert its[1] <= 2 * its[0] and its[2] <= 2 * its[1]
+
+
+# --------------------------------------------------------------------------
+# slab-by-slab Delta product, recovery and residual (Section II-B)
+# --------------------------------------------------------------------------
+
+SLAB_CASES = [(3, 4, 5, 2, 1), (4, 5, 6, 3, 2), (1, 3, 4, 2, 2), (2, 1, 3, 1, 1), (5, 7, 2, 4, 2)]
+
+
+@pytest.mark.parametrize("shape", SLAB_CASES)
+def test_slab_delta_product_matches_assembled_delta(shape):
+    """The slab-by-slab product against scipy's assembled
+    A~ Q~^-1 A~' + B~ R~^-1 B~' (odd and even N, K = 1, N = 1), with and
+    without boundary terms in omega~."""
+    K, N, T, n, m = shape
+    g = synth.random_grid(K, N, T, n, m, seed=sum(shape))
+    rng = np.random.default_rng(7)
+    for w in (None, rng.standard_normal((T, K * N, n))):
+        P = as_problem(g, w)
+        orc = O.Oracle(P)
+        b = O.slab_blocks(P)
+        for trial in range(2):
+            vec = rng.standard_normal(P.dim_x)
+            want = orc.Delta @ vec
+            got = O.delta_apply_slabs(P, vec, b).ravel()
+            assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+        assert np.array_equal(O.rhs_slabs(P).ravel(), orc.r_delta)
+
+
+@pytest.mark.parametrize("shape", SLAB_CASES[:3])
+def test_slab_recovery_and_residual_match_the_assembled_forms(shape):
+    K, N, T, n, m = shape
+    g = synth.random_grid(K, N, T, n, m, seed=10 + sum(shape))
+    P = as_problem(g)
+    orc = O.Oracle(P)
+    sol = orc.solve(1e-12)
+    x, u = O.recover(orc.S, sol.delta.ravel())
+    xs, us = O.recover_slabs(P, sol.delta)
+    assert np.abs(xs.ravel() - x).max() <= 1e-13 * np.abs(x).max()
+    assert np.abs(us.ravel() - u).max() <= 1e-13 * np.abs(u).max()
+    # the true residual of the converged solve and of a perturbed iterate
+    res = O.true_residual_slabs(P, sol.delta)
+    want = np.linalg.norm(orc.r_delta - orc.Delta @ sol.delta.ravel()) / np.linalg.norm(orc.r_delta)
+    assert res <= 1e-11 and abs(res - want) <= 1e-13
+    bad = sol.delta.copy()
+    bad[T // 2, 0, 0] += 1.0
+    assert O.true_residual_slabs(P, bad) > 1e-3
+
+
+def test_slab_recovery_is_feasible_under_simulation():
+    """x and u from the slab recovery satisfy the grid dynamics node by node
+    (the simulator of eq. 2d_graph_dynamics), independent of the stacked
+    assembly."""
+    g = synth.random_grid(4, 3, 6, 2, 1, seed=77)
+    P = as_problem(g)
+    sol = O.Oracle(P).solve_direct()
+    x, u = O.recover_slabs(P, sol.delta)
+    sim = simulate(P, u.reshape(P.T, P.nodes, P.m))
+    assert np.abs(sim - x.reshape(sim.shape)).max() <= 1e-10 * max(1.0, np.abs(sim).max())
+
+
+def test_cg_iteration_bound_golden_values():
+    """The smallest k with 2((sqrt kappa - 1)/(sqrt kappa + 1))^k <= reduction
+    (Section III's CG bound, reading A13), worked by hand:
+      kappa = 100, 1e-6: rate 9/11, k >= ln(5e-7)/ln(9/11) = 72.30 -> 73
+      kappa = 4,   1e-6: rate 1/3,  k >= ln(5e-7)/ln(1/3)  = 13.21 -> 14
+      kappa = 100, 1e-3: k >= ln(5e-4)/ln(9/11) = 37.88 -> 38
+      kappa = 1e4, 1e-8: rate 99/101, k >= ln(5e-9)/ln(99/101) = 955.7 -> 956
+    and each value is checked to be the smallest that satisfies the bound."""
+    for kappa, red, k in ((100.0, 1e-6, 73), (4.0, 1e-6, 14), (100.0, 1e-3, 38), (1e4, 1e-8, 956)):
+        assert O.cg_iteration_bound(kappa, red) == k
+        rate = (math.sqrt(kappa) - 1.0) / (math.sqrt(kappa) + 1.0)
+        assert 2.0 * rate ** k <= red < 2.0 * rate ** (k - 1)
+    assert O.cg_iteration_bound(1.0, 1e-6) == 1
