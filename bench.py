@@ -1,6 +1,8 @@
 """Benchmark of the lq2d solver: PCG iterations/s and time-to-solve at a
-1e-8 relative KKT residual, on the K = N = 64, n = 4, m = 2, T = 100
-synthetic grid (S = L = 2, FP64).
+1e-8 relative KKT residual, on the K = N = 256, n = 4, m = 2, T = 200
+synthetic grid (52.7 M multipliers, S = L = 2, FP64), the largest
+single-GPU workload; the K = N = 64, T = 100 grid is measured beside it with
+the same protocol.
 
 One step = one full pass of the method over the resident problem: the setup
 (inverses, splitting blocks, banded block-Cholesky factors of Phi_bar), the
@@ -47,7 +49,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="grid64_T100", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="grid256_T200", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--also", default="grid64_T100",
+                    help="second workload measured with the same protocol (FP64, modes 1 and 2, roofline) and "
+                         "reported under its own key; 'none' to skip")
+    ap.add_argument("--aux-steps", type=int, default=5,
+                    help="steps of the passes beside the timed region (per-launch timing, precision comparison, "
+                         "end to end), at most --steps")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--driver", choices=["graph", "stream"], default="graph")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed2"], default="fp64",
@@ -266,10 +274,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "nbjm_sweep_%s.md" % workload)
+def profiled_traffic(workload, precision="fp64"):
+    """DRAM bytes per sweep launch from the committed ncu summary of that
+    workload and sweep precision, if it was taken on the current kernel
+    source (else None)."""
+    name = "nbjm_sweep_%s.md" % workload if precision == "fp64" else "nbjm_sweep_f32_%s.md" % workload
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -283,6 +293,9 @@ def profiled_traffic(workload):
 # --------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, single-threaded, bounded sample
 # --------------------------------------------------------------------------
+
+# workloads whose explicit Delta the assembled oracle can hold
+ASSEMBLED_ORACLE_FITS = ("grid4_T20", "grid64_T100")
 
 CPU_SCRIPT = r"""
 import json, sys, time
@@ -368,173 +381,227 @@ def run_ours(args, dist):
     dev = torch.device("cuda", dist.local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    g = synth.workload(args.workload)
-    host = [np.ascontiguousarray(a) for a in g.arrays()]
-    inputs = [torch.from_numpy(a).to(dev) for a in host]
-    pinned = [torch.from_numpy(a).pin_memory() for a in host]
-    prob = lq2d.Problem.from_device(g.K, g.N, g.T, g.n, g.m, *inputs, stream=stream)
-    if args.precision != "fp64":
-        prob.set_precision(1 if args.precision == "mixed" else 2)
-    if args.driver == "stream":
-        prob.set_option(lq2d.OPT_DRIVER, 1)
-    x = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
-    u = torch.empty((g.T, g.nodes, g.m), dtype=torch.float64, device=dev)
-    lam = torch.empty_like(x)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    max_iter = 100000
+    aux = max(1, min(args.aux_steps, args.steps))
 
-    def step():
-        prob.update_device(*inputs, stream=stream)
-        out = prob.solve_device(args.tol, 2, 2, max_iter, x=x, u=u, costate=lam, stream=stream)
-        return out
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    def timed(nsteps):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
-        its, rls = [], []
-        for k in range(nsteps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            out = step()
-            evs[k][1].record(stream)
-            its.append(out["iterations"])
-            rls.append(out["rel_kkt"])
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in evs], its, rls
-
-    # ---- timed region: K steps, L2 flushed before each, device events per step
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = None
-    clocks = Clocks(uuid)
-    launches0 = prob.stats()["launches_total"]
-    clocks.start()
-    torch.cuda.synchronize()
-    dist.barrier()
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    step_ms, iters, rels = timed(args.steps)
-    dist.barrier()
-    torch.cuda.synchronize()
-    w1 = time.perf_counter()
-    clk = clocks.stop()
-    launches = prob.stats()["launches_total"] - launches0
-    dev_ms = sum(step_ms)
-    tot_iters = sum(iters)
+
+    def measure(workload, headline):
+        """The protocol on one workload: the timed region (K steps, device
+        events, L2 flushed before each), the per-launch roofline pass, the
+        precision comparison and, for the headline, the end-to-end pass."""
+        g = synth.workload(workload)
+        host = [np.ascontiguousarray(a) for a in g.arrays()]
+        inputs = [torch.from_numpy(a).to(dev) for a in host]
+        prob = lq2d.Problem.from_device(g.K, g.N, g.T, g.n, g.m, *inputs, stream=stream)
+        if args.precision != "fp64":
+            prob.set_precision(1 if args.precision == "mixed" else 2)
+        if args.driver == "stream":
+            prob.set_option(lq2d.OPT_DRIVER, 1)
+        x = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
+        u = torch.empty((g.T, g.nodes, g.m), dtype=torch.float64, device=dev)
+        lam = torch.empty_like(x)
+        max_iter = 100000
+
+        def step():
+            prob.update_device(*inputs, stream=stream)
+            return prob.solve_device(args.tol, 2, 2, max_iter, x=x, u=u, costate=lam, stream=stream)
+
+        def timed(nsteps):
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(nsteps)]
+            its, rls = [], []
+            for k in range(nsteps):
+                flush.zero_()
+                evs[k][0].record(stream)
+                out = step()
+                evs[k][1].record(stream)
+                its.append(out["iterations"])
+                rls.append(out["rel_kkt"])
+            torch.cuda.synchronize()
+            return [a.elapsed_time(b) for a, b in evs], its, rls
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+
+        # ---- timed region
+        res = {"g": g}
+        clocks = Clocks(uuid) if headline else None
+        launches0 = prob.stats()["launches_total"]
+        if clocks:
+            clocks.start()
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        step_ms, iters, rels = timed(args.steps)
+        dist.barrier()
+        torch.cuda.synchronize()
+        w1 = time.perf_counter()
+        res["clocks"] = clocks.stop() if clocks else None
+        res["launches"] = prob.stats()["launches_total"] - launches0
+        res["dev_ms"] = sum(step_ms)
+        res["iters"] = iters
+        res["rels"] = rels
+        res["wall_ms"] = (w1 - w0) * 1e3
+
+        # ---- roofline of the dominant kernel (NBJM sweep): per-launch events
+        # on the solve stream, over `aux` steps run again with timing on
+        prob.set_option(lq2d.OPT_TIMING, 1)
+        sweep_ms, sweep_launches, delta_ms, delta_launches, fl_total, by_total = 0.0, 0, 0.0, 0, 0, 0
+        fl = sweep_flops(g)
+        for _ in range(aux):
+            flush.zero_()
+            out = step()
+            st = prob.stats()
+            sweep_ms += st["sweep_ms"]
+            sweep_launches += st["sweep_launches"]
+            delta_ms += st["delta_ms"]
+            delta_launches += st["delta_launches"]
+            fl_total += sweep_flops_of_solve(fl, out["iterations"])
+            by_total += sweep_bytes_of_solve(g, out["iterations"])
+        prob.set_option(lq2d.OPT_TIMING, 0)
+        measured_note = ("CUDA events around each sweep launch on the solve stream, a second pass over %d steps "
+                         "of the same workload" % aux)
+        if args.precision == "fp64":
+            achieved = fl_total / (sweep_ms / 1e3) / 1e12
+            res["roofline"] = {
+                "kernel": "nbjm_sweep_kernel<4,*,double>", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": profiled_traffic(workload, "fp64"),
+                "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
+                "flops_per_launch": fl_total / max(sweep_launches, 1),
+                "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "measured": measured_note,
+                "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
+            }
+        else:
+            peak = measured_hbm_gbs()
+            achieved = by_total / (sweep_ms / 1e3) / 1e9
+            res["roofline"] = {
+                "kernel": "nbjm_sweep_kernel<4,*,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(workload, "fp32"),
+                "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
+                "bytes_per_launch": by_total / max(sweep_launches, 1),
+                "fp32_tflops": fl_total / (sweep_ms / 1e3) / 1e12,
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "measured": measured_note,
+                "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
+            }
+
+        # ---- the same workload in the other precisions, same protocol; the
+        # FP32 sweep's roofline (bytes against the copy bandwidth) beside it
+        compare = None
+        if not args.no_compare and args.precision == "fp64":
+            compare = []
+            for mode, label in ((1, "mixed: FP32 preconditioner, FP64 residual/dots/updates"),
+                                (2, "mixed2: FP32 preconditioner and Delta product, FP64 residual replacement")):
+                prob.set_precision(mode)
+                for _ in range(args.warmup):
+                    step()
+                c_ms, c_its, c_rels = timed(aux)
+                c_dev = sum(c_ms)
+                entry = {"precision": label, "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT,
+                         "ms_per_step": c_dev / aux, "steps": aux,
+                         "iterations_per_solve": sum(c_its) / len(c_its), "rel_kkt_residual": max(c_rels),
+                         "speedup_time_to_solve": (res["dev_ms"] / args.steps) / (c_dev / aux)}
+                prob.set_option(lq2d.OPT_TIMING, 1)
+                s_ms, s_n, b_tot = 0.0, 0, 0
+                for _ in range(min(aux, 3)):
+                    flush.zero_()
+                    out = step()
+                    st = prob.stats()
+                    s_ms += st["sweep_ms"]
+                    s_n += st["sweep_launches"]
+                    b_tot += sweep_bytes_of_solve(g, out["iterations"])
+                prob.set_option(lq2d.OPT_TIMING, 0)
+                peak = measured_hbm_gbs()
+                ach = b_tot / (s_ms / 1e3) / 1e9
+                entry["sweep_roofline"] = {"kernel": "nbjm_sweep_kernel<4,*,float>", "bound": "hbm",
+                                           "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                           "traffic": profiled_traffic(workload, "fp32"),
+                                           "avg_launch_ms": s_ms / max(s_n, 1),
+                                           "bytes_per_launch": b_tot / max(s_n, 1)}
+                compare.append(entry)
+            prob.set_precision(0)
+        res["compare"] = compare
+
+        # ---- end to end: host (pinned) inputs in, host outputs back, per step
+        if headline:
+            pinned = [torch.from_numpy(a).pin_memory() for a in host]
+            xh = np.empty((g.T + 1, g.nodes, g.n))
+            uh = np.empty((g.T, g.nodes, g.m))
+            lh = np.empty_like(xh)
+            res["h2d"] = sum(a.nbytes for a in host)
+            res["d2h"] = xh.nbytes + uh.nbytes + lh.nbytes
+            torch.cuda.synchronize()
+            e_iters = 0
+            e0 = time.perf_counter()
+            for _ in range(aux):
+                flush.zero_()
+                torch.cuda.synchronize()
+                prob.update(*[p.data_ptr() for p in pinned])
+                out = prob.solve(args.tol, 2, 2, max_iter, out=(xh, uh, lh))
+                e_iters += out["iterations"]
+            e1 = time.perf_counter()
+            res["e2e_value"] = dist.reduce(e_iters, "sum") / dist.reduce(e1 - e0, "max")
+            res["e2e_steps"] = aux
+        prob.close()
+        del inputs, x, u, lam
+        torch.cuda.empty_cache()
+        return res
+
+    main = measure(args.workload, True)
+    g = main["g"]
+    tot_iters = sum(main["iters"])
     all_iters = dist.reduce(tot_iters, "sum")
-    max_ms = dist.reduce(dev_ms, "max")
+    max_ms = dist.reduce(main["dev_ms"], "max")
     value = all_iters / (max_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (NBJM sweep): per-launch events on
-    # the solve stream, over the same K steps run again with timing on
-    prob.set_option(lq2d.OPT_TIMING, 1)
-    sweep_ms, sweep_launches, delta_ms, delta_launches, fl_total, by_total = 0.0, 0, 0.0, 0, 0, 0
-    fl = sweep_flops(g)
-    for _ in range(args.steps):
-        flush.zero_()
-        out = step()
-        st = prob.stats()
-        sweep_ms += st["sweep_ms"]
-        sweep_launches += st["sweep_launches"]
-        delta_ms += st["delta_ms"]
-        delta_launches += st["delta_launches"]
-        fl_total += sweep_flops_of_solve(fl, out["iterations"])
-        by_total += sweep_bytes_of_solve(g, out["iterations"])
-    prob.set_option(lq2d.OPT_TIMING, 0)
-    measured_note = ("CUDA events around each sweep launch on the solve stream, second pass over the same %d steps"
-                     % args.steps)
-    if args.precision == "fp64":
-        achieved = fl_total / (sweep_ms / 1e3) / 1e12
-        roofline = {
-            "kernel": "nbjm_sweep_kernel<4,*,double>", "bound": "alu", "achieved": achieved,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": profiled_traffic(args.workload),
-            "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
-            "flops_per_launch": fl_total / max(sweep_launches, 1),
-            "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-            "measured": measured_note,
-            "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
-        }
-    else:
-        peak = measured_hbm_gbs()
-        achieved = by_total / (sweep_ms / 1e3) / 1e9
-        roofline = {
-            "kernel": "nbjm_sweep_kernel<4,*,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-            "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
-            "bytes_per_launch": by_total / max(sweep_launches, 1),
-            "fp32_tflops": fl_total / (sweep_ms / 1e3) / 1e12,
-            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "measured": measured_note,
-            "delta_apply_ms_per_launch": delta_ms / max(delta_launches, 1),
-        }
-
-    # ---- the same workload in the other precision, same protocol (FP64 plain vs mixed)
-    compare = None
-    if not args.no_compare and args.precision == "fp64":
-        compare = []
-        for mode, label in ((1, "mixed: FP32 preconditioner, FP64 residual/dots/updates"),
-                            (2, "mixed2: FP32 preconditioner and Delta product, FP64 residual replacement")):
-            prob.set_precision(mode)
-            for _ in range(args.warmup):
-                step()
-            c_ms, c_its, c_rels = timed(args.steps)
-            c_dev = sum(c_ms)
-            compare.append({"precision": label, "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT,
-                            "ms_per_step": c_dev / args.steps, "iterations_per_solve": sum(c_its) / len(c_its),
-                            "rel_kkt_residual": max(c_rels), "speedup_time_to_solve": dev_ms / c_dev})
-        prob.set_precision(0)
-
-    # ---- end to end: host (pinned) inputs in, host outputs back, per step
-    xh = np.empty((g.T + 1, g.nodes, g.n))
-    uh = np.empty((g.T, g.nodes, g.m))
-    lh = np.empty_like(xh)
-    h2d = sum(a.nbytes for a in host)
-    d2h = xh.nbytes + uh.nbytes + lh.nbytes
-    torch.cuda.synchronize()
-    e_iters = 0
-    e0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        prob.update(*[p.data_ptr() for p in pinned])
-        out = prob.solve(args.tol, 2, 2, max_iter, out=(xh, uh, lh))
-        e_iters += out["iterations"]
-    e1 = time.perf_counter()
-    e2e_value = dist.reduce(e_iters, "sum") / dist.reduce(e1 - e0, "max")
-    prob.close()
+    second = None
+    if args.also and args.also != "none" and args.also != args.workload:
+        o = measure(args.also, False)
+        og = o["g"]
+        second = {"workload": args.also, "K": og.K, "N": og.N, "T": og.T, "n": og.n, "m": og.m,
+                  "value": sum(o["iters"]) / (o["dev_ms"] / 1e3), "unit": UNIT, "steps": args.steps,
+                  "time_to_solve_ms": o["dev_ms"] / args.steps,
+                  "iterations_per_solve": sum(o["iters"]) / len(o["iters"]), "rel_kkt_residual": max(o["rels"]),
+                  "roofline": o["roofline"], "compare_precision": o["compare"]}
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, args.cpu_iters)
+        cpu = cpu_baseline(args.workload if args.workload in ASSEMBLED_ORACLE_FITS else "grid64_T100",
+                           args.cpu_iters)
 
     if dist.rank == 0:
-        mean_iters = tot_iters / len(iters)
+        mean_iters = tot_iters / len(main["iters"])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": main["dev_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "K": g.K, "N": g.N, "T": g.T, "n": g.n, "m": g.m, "S": 2,
                        "L": 2, "tol": args.tol, "precision": args.precision, "driver": args.driver,
                        "l2": "flushed before each step (256 MiB write, outside the step events)",
                        "parallelism": "replicas" if dist.world > 1 else "single"},
-            "time_to_solve_ms": dev_ms / args.steps,
+            "time_to_solve_ms": main["dev_ms"] / args.steps,
             "iterations_per_solve": mean_iters,
-            "rel_kkt_residual": max(rels),
-            "wall_ms": (w1 - w0) * 1e3,
-            "roofline": roofline,
-            "compare_precision": compare,
+            "rel_kkt_residual": max(main["rels"]),
+            "wall_ms": main["wall_ms"],
+            "roofline": main["roofline"],
+            "compare_precision": main["compare"],
+            "also": second,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "clocks": clk,
-            "gpu_launches": launches,
+            "e2e": {"value": main["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": main["h2d"],
+                    "d2h_bytes_per_step": main["d2h"], "steps": main["e2e_steps"]},
+            "clocks": main["clocks"],
+            "gpu_launches": main["launches"],
         }
         print(json.dumps(line), flush=True)
 
