@@ -64,7 +64,8 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed mixed-precision comparison on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG steps in the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG steps in the all-cores CPU sample")
+    ap.add_argument("--cpu-iters-one", type=int, default=1, help="oracle PCG steps in the one-thread CPU sample")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many uneven instances (K, N in 8..64, T in 50..200) "
                          "against solving them one after another")
@@ -294,41 +295,90 @@ def profiled_traffic(workload, precision="fp64"):
 # CPU baseline: the oracle as it stands, single-threaded, bounded sample
 # --------------------------------------------------------------------------
 
-# workloads whose explicit Delta the assembled oracle can hold
-ASSEMBLED_ORACLE_FITS = ("grid4_T20", "grid64_T100")
+def host_cores():
+    """Cores this process may run on, and how many oracle worker processes
+    the host's free memory allows (each holds about 1.5 GB of splitting
+    blocks at the 256 x 256 x 200 size)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    try:
+        avail_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 1e9
+    except (ValueError, OSError):
+        avail_gb = 1e9
+    return cores, max(1, min(cores, int(avail_gb / 3.0)))
+
 
 CPU_SCRIPT = r"""
 import json, sys, time
 sys.path.insert(0, %(root)r)
 from oracle import lq2d_oracle as O
+from oracle import slab_pcg as SP
 from paper_2304_04980_gb300 import synth
-g = synth.workload(%(workload)r)
-t0 = time.perf_counter()
-orc = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays()))
-pre = orc.preconditioner(2, 2)
-t1 = time.perf_counter()
-res = O.pcg(orc.Delta, orc.r_delta, pre.apply, 1e-300, %(iters)d, confirm_true_residual=False)
-t2 = time.perf_counter()
-print(json.dumps({"setup_s": t1 - t0, "iters": res.iterations, "loop_s": t2 - t1}))
+
+
+def main():
+    g = synth.workload(%(workload)r)
+    P = O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())
+    t0 = time.perf_counter()
+    so = SP.SlabOracle(P, workers=%(workers)d)
+    t1 = time.perf_counter()
+    clock = []
+    so.solve(1e-300, 2, 2, %(iters)d, confirm_true_residual=False, step_clock=clock)
+    so.close()
+    print(json.dumps({"setup_s": t1 - t0, "iters": len(clock) - 1, "loop_s": clock[-1] - clock[0],
+                      "clock": clock}))
+
+
+if __name__ == "__main__":
+    main()
 """
 
 
-def cpu_baseline(workload, iters):
+def run_oracle_steps(workload, workers, iters, timeout=1800):
+    """The oracle's Algorithm 1 loop (slab form, S = L = 2) for `iters`
+    passes on the full workload, in a subprocess with `workers` processes
+    and one BLAS thread each; returns the parsed timing record or a failure
+    string."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = CPU_SCRIPT % {"root": ROOT, "workload": workload, "iters": iters}
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    code = CPU_SCRIPT % {"root": ROOT, "workload": workload, "iters": iters, "workers": workers}
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
     if out.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "failed: " + out.stderr.strip().splitlines()[-1][:200] if out.stderr else "failed"}
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": r["iters"] / r["loop_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d PCG steps (Algorithm 1 loop, S=L=2) of the oracle on the full %s problem, "
-                      "single thread; oracle setup (assembly, splitting, banded Cholesky) %.1f s not counted"
-                      % (r["iters"], workload, r["setup_s"]),
-            "setup_s": r["setup_s"], "loop_s": r["loop_s"]}
+        tail = out.stderr.strip().splitlines()[-1][:200] if out.stderr.strip() else "exit %d" % out.returncode
+        return "failed: " + tail
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload, iters_all, iters_one):
+    """The oracle timed on the host: on all cores this process may use
+    (the slabs split over worker processes), and on one thread."""
+    cores, workers = host_cores()
+    res = {"unit": UNIT, "kind": "oracle"}
+    r = run_oracle_steps(workload, workers, iters_all)
+    if isinstance(r, str):
+        res.update({"value": None, "cores": workers, "sample": r})
+    else:
+        res.update({"value": r["iters"] / r["loop_s"], "cores": workers, "host_cores": cores,
+                    "sample": "%d PCG steps (Algorithm 1 loop, S = L = 2, every step timed after the initial "
+                              "residual and preconditioner) of the slab-by-slab oracle on the full %s problem, "
+                              "%d worker processes splitting the time slabs, one BLAS thread each; oracle "
+                              "setup (blocks, splitting, banded Cholesky per column pair) %.1f s not counted"
+                              % (r["iters"], workload, workers, r["setup_s"]),
+                    "setup_s": r["setup_s"], "loop_s": r["loop_s"]})
+    r1 = run_oracle_steps(workload, 1, iters_one)
+    if isinstance(r1, str):
+        res["single_thread"] = {"value": None, "cores": 1, "sample": r1}
+    else:
+        res["single_thread"] = {
+            "value": r1["iters"] / r1["loop_s"], "unit": UNIT, "cores": 1,
+            "sample": "%d PCG step(s) of the same oracle on the full %s problem, one process, one BLAS thread; "
+                      "setup %.1f s not counted" % (r1["iters"], workload, r1["setup_s"]),
+            "setup_s": r1["setup_s"], "loop_s": r1["loop_s"]}
+    return res
 
 
 # --------------------------------------------------------------------------
@@ -336,33 +386,32 @@ def cpu_baseline(workload, iters):
 # --------------------------------------------------------------------------
 
 def run_reference(args, dist):
+    """The paper ships no code, so the reference arm is the CPU oracle as it
+    stands (slab form), on all host cores, on this arm's workload: one
+    Algorithm 1 loop of W + K passes, the last K timed step by step."""
     if dist.rank != 0:
         return
-    from oracle import lq2d_oracle as O
+    cores, workers = host_cores()
     g = synth.workload(args.workload)
-    orc = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays()))
-    pre = orc.preconditioner(2, 2)
-    per_step = 2
-
-    def step():
-        res = O.pcg(orc.Delta, orc.r_delta, pre.apply, 1e-300, per_step, confirm_true_residual=False)
-        return res.iterations
-
-    for _ in range(args.warmup):
-        O.pcg(orc.Delta, orc.r_delta, pre.apply, 1e-300, 1, confirm_true_residual=False)
-    t0 = time.perf_counter()
-    its = sum(step() for _ in range(args.steps))
-    t1 = time.perf_counter()
-    value = its / (t1 - t0)
+    r = run_oracle_steps(args.workload, workers, args.warmup + args.steps, timeout=3600)
+    if isinstance(r, str):
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run " + r}), flush=True)
+        return
+    clock = r["clock"]
+    t_steps = clock[args.warmup + args.steps] - clock[args.warmup]
+    value = args.steps / t_steps
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": (t1 - t0) * 1e3 / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_steps * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "K": g.K, "N": g.N, "T": g.T, "n": g.n, "m": g.m, "S": 2, "L": 2,
-                   "tol": args.tol, "precision": "fp64"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step = %d PCG steps of the CPU oracle (numpy/scipy, as it stands) on the "
-                                   "full problem; oracle setup not timed" % per_step},
+                   "tol": args.tol, "precision": "fp64", "driver": "cpu oracle",
+                   "l2": "not applicable (host)", "parallelism": "%d host processes" % workers},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "host_cores": cores, "kind": "oracle",
+                         "sample": "each step = one PCG step (Algorithm 1 loop pass, S = L = 2) of the slab-by-slab "
+                                   "CPU oracle (numpy/scipy, as it stands) on the full problem, %d worker "
+                                   "processes; oracle setup %.1f s and the initial residual not timed"
+                                   % (workers, r["setup_s"])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -576,8 +625,7 @@ def run_ours(args, dist):
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload if args.workload in ASSEMBLED_ORACLE_FITS else "grid64_T100",
-                           args.cpu_iters)
+        cpu = cpu_baseline(args.workload, args.cpu_iters, args.cpu_iters_one)
 
     if dist.rank == 0:
         mean_iters = tot_iters / len(main["iters"])

@@ -439,12 +439,16 @@ class PCGResult:
 
 def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray], np.ndarray],
         tol: float, max_iter: int, delta0: Optional[np.ndarray] = None,
-        stop: str = "rel2", confirm_true_residual: bool = True) -> PCGResult:
+        stop: str = "rel2", confirm_true_residual: bool = True,
+        step_clock: Optional[list] = None) -> PCGResult:
     """Algorithm 1.  `stop` selects reading A9: "rel2" stops when
     ||r||_2 <= tol ||r_delta||_2, "absinf" when ||r||_inf < tol (the paper's
     test).  With confirm_true_residual the exit is re-checked on
     r_delta - Delta delta and the iteration restarts from the current delta
-    if that check fails (reading A9)."""
+    if that check fails (reading A9).  A list passed as step_clock receives
+    time.perf_counter() before the first pass of the loop and after every
+    pass (a timing aid; it changes no arithmetic)."""
+    import time
     bnorm = np.linalg.norm(r_delta)
 
     def passed(r):
@@ -467,6 +471,8 @@ def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray
         d = precond(r)                                    # first direction
         mu = d @ r
         converged = False
+        if step_clock is not None:
+            step_clock.append(time.perf_counter())
         while it < max_iter:
             y = Delta @ d                                 # operator product
             theta = mu / (y @ d)                          # step length
@@ -483,6 +489,8 @@ def pcg(Delta: sp.csr_matrix, r_delta: np.ndarray, precond: Callable[[np.ndarray
             betas.append(mu_new / mu)
             d = q + (mu_new / mu) * d                     # next direction
             mu = mu_new
+            if step_clock is not None:
+                step_clock.append(time.perf_counter())
         if not converged:
             return PCGResult(delta, it, False, hist, restarts, alphas, betas)
         if not confirm_true_residual or passed(r_delta - Delta @ delta):

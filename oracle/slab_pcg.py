@@ -88,6 +88,10 @@ class SlabSplitting:
         # banded Cholesky factor of every (class, v) block of Phi_hat
         V = (P.N + 1) // 2
         self.groups = [np.flatnonzero(v == vv) for vv in range(V)]
+        # the slab's unknowns listed pair by pair: block g of Phi_hat is the
+        # contiguous run bounds[g] .. bounds[g+1] of this order
+        self.perm = np.concatenate(self.groups)
+        self.bounds = np.cumsum([0] + [len(g) for g in self.groups])
         self.factors = {}
         for c, cb in self.cls.items():
             fs = []
@@ -114,11 +118,13 @@ class SlabSplitting:
         out = np.empty_like(tau)
         for c, ts in self.slab_classes(t0, t1).items():
             rows = np.asarray(ts) - t0
-            X = tau[rows].T
+            X = np.ascontiguousarray(tau[rows][:, self.perm].T)   # [pair-ordered unknown, slab]
             Y = np.empty_like(X)
-            for g, cf in zip(self.groups, self.factors[c]):
-                Y[g] = sla.cho_solve_banded((cf, True), X[g])
-            out[rows] = Y.T
+            for a, b, cf in zip(self.bounds[:-1], self.bounds[1:], self.factors[c]):
+                Y[a:b] = sla.cho_solve_banded((cf, True), X[a:b], check_finite=False)
+            res = np.empty((len(rows), X.shape[0]))
+            res[:, self.perm] = Y.T
+            out[rows] = res
         return out
 
     def omega_apply(self, theta: np.ndarray, t0: int, t1: int) -> np.ndarray:
@@ -260,16 +266,20 @@ class SlabOracle:
             A["delta_s"][...] = A[cur]                         # delta^(s+1) = theta^(L)
         return A["delta_s"].ravel().copy()
 
-    def solve(self, tol: float, S: int = 2, L: int = 2, max_iter: int = 10000,
-              confirm_true_residual: bool = True) -> O.PCGResult:
+    def operator(self):
+        """Delta as an object with `@`, for lq2d_oracle.pcg."""
         oracle = self
 
         class _Delta:
             def __matmul__(self, v):
                 return oracle.delta_apply(v)
 
-        return O.pcg(_Delta(), self.r_delta, lambda r: self.precondition(r, S, L), tol, max_iter,
-                     confirm_true_residual=confirm_true_residual)
+        return _Delta()
+
+    def solve(self, tol: float, S: int = 2, L: int = 2, max_iter: int = 10000,
+              confirm_true_residual: bool = True, step_clock: Optional[list] = None) -> O.PCGResult:
+        return O.pcg(self.operator(), self.r_delta, lambda r: self.precondition(r, S, L), tol, max_iter,
+                     confirm_true_residual=confirm_true_residual, step_clock=step_clock)
 
     def close(self):
         if self.pool is not None:
