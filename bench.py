@@ -83,6 +83,10 @@ def parse_args():
     ap.add_argument("--multirhs", type=int, default=0,
                     help="multi-right-hand-side solve: this many instances of the batch family (K, N in 8..64, "
                          "T in 50..200), each with 32 initial states x0 ~ N(0, 1), against single solves")
+    ap.add_argument("--mrhs-apply", type=int, default=0,
+                    help="apply the 32-right-hand-side tensor-core preconditioner (S = L = 2) this many times on "
+                         "--workload and print its time per application (the launch sequence profiled for the "
+                         "multi-right-hand-side sweep)")
     return ap.parse_args()
 
 
@@ -672,22 +676,42 @@ def run_batch(args, dist):
             p.set_precision(1 if args.precision == "mixed" else 2)
     batch = lq2d.Batch(probs)
     unknowns = sum(gr.nodes * (gr.T + 1) * gr.n for gr in grids)
+    tuned = None
+    if args.precision == "fp64":
+        tuned = batch.autotune(2, 2, 3, stream=stream)
     for _ in range(args.warmup):
         batch.solve(args.tol, 2, 2, 100000, stream=stream)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    its = 0
+    persistent = batch.get_option(lq2d.BATCH_USES_PERSISTENT)
+
+    def timed_batch(nsteps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        its = 0
+        for k in range(nsteps):
+            ev[k][0].record(stream)
+            out = batch.solve(args.tol, 2, 2, 100000, stream=stream)
+            ev[k][1].record(stream)
+            its += sum(out["iterations"])
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), its
+
     launches0 = sum(p.stats()["launches_total"] for p in probs)
-    for k in range(args.steps):
-        ev[k][0].record(stream)
-        out = batch.solve(args.tol, 2, 2, 100000, stream=stream)
-        ev[k][1].record(stream)
-        its += sum(out["iterations"])
-    torch.cuda.synchronize()
-    b_ms = sum(a.elapsed_time(b) for a, b in ev)
+    b_ms, its = timed_batch(args.steps)
     launches = sum(p.stats()["launches_total"] for p in probs) - launches0
-    # the same instances one after another (one graph launch each)
-    for p in probs[:4]:
+    # the same batch as one chain per problem in the graph (no persistent loop)
+    chains = None
+    if persistent:
+        batch.set_option(lq2d.BATCH_PERSISTENT, 0)
+        batch.solve(args.tol, 2, 2, 100000, stream=stream)
+        c_ms, _ = timed_batch(max(1, min(args.steps, 2)))
+        chains = {"ms_per_solve": c_ms / max(1, min(args.steps, 2)),
+                  "speedup_persistent_vs_chains": (c_ms / max(1, min(args.steps, 2))) / (b_ms / args.steps)}
+        batch.set_option(lq2d.BATCH_PERSISTENT, 1)
+        if tuned is not None:
+            batch.set_option(lq2d.BATCH_THREADS, tuned[0])
+    # the same instances one after another (one graph launch each; every
+    # problem's own graph is built by an untimed solve first)
+    for p in probs:
         p.solve_device(args.tol, 2, 2, 100000, stream=stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -707,6 +731,10 @@ def run_batch(args, dist):
         "config": {"workload": "batch%d: K, N in 8..64, T in 50..200, n = 4, m = 2, coupling in 0.02..0.2" % len(probs),
                    "precision": args.precision, "tol": args.tol, "S": 2, "L": 2, "unknowns": unknowns},
         "pcg_iters_per_s": its / (b_ms / 1e3),
+        "persistent_loop": bool(persistent),
+        "autotuned_threads": None if tuned is None else tuned[0],
+        "autotune_dsr_ms": None if tuned is None else tuned[1],
+        "chains": chains,
         "sequential": {"ms_for_all": s_ms, "instances_per_s": len(probs) / (s_ms / 1e3), "iterations": s_its},
         "speedup_vs_sequential": s_ms / (b_ms / args.steps),
         "gpu_launches": launches,
@@ -914,8 +942,40 @@ def run_multirhs(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_mrhs_apply(args):
+    """D_S r of 32 right-hand sides at once (lq2d_apply_precond_multi_device),
+    `args.mrhs_apply` times after one untimed application."""
+    import torch
+
+    from paper_2304_04980_gb300 import lq2d
+
+    lq2d.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = synth.workload(args.workload)
+    prob = lq2d.Problem.from_grid(g)
+    r = torch.from_numpy(synth.random_vector((32, g.T + 1, g.nodes, g.n), seed=7)).to(dev)
+    q = torch.empty_like(r)
+    prob.apply_precond_multi_device(32, 2, 2, r, q, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.mrhs_apply):
+        prob.apply_precond_multi_device(32, 2, 2, r, q, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.mrhs_apply, 1)
+    print(json.dumps({"metric": "32-right-hand-side D_S r (ms per application)", "value": ms, "unit": "ms",
+                      "config": {"workload": args.workload, "rhs": 32, "S": 2, "L": 2},
+                      "applications": args.mrhs_apply}), flush=True)
+    prob.close()
+
+
 def main():
     args = parse_args()
+    if args.mrhs_apply > 0:
+        run_mrhs_apply(args)
+        return
     if args.warmstart > 0:
         run_warmstart(args, Dist())
         return

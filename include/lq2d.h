@@ -75,12 +75,18 @@ enum {
                                   extreme eigenvalues of the preconditioned operator (Lanczos
                                   matrix of CG; Section V reports kappa before and after
                                   preconditioning); read them with lq2d_get_stats */
-  LQ2D_OPT_SWEEP_THREADS = 7  /* 32, 64, 128 or 256: threads per CTA of the NBJM sweeps, i.e. a
+  LQ2D_OPT_SWEEP_THREADS = 7, /* 32, 64, 128 or 256: threads per CTA of the NBJM sweeps, i.e. a
                                   tile of threads/g time steps per CTA (g = 2n rounded up to a
                                   power of two); sets the FP64 and FP32 sweeps alike.
                                   Default 64; lq2d_autotune picks it by timing.  Results may
                                   differ in the last bits between widths (partial sums are
                                   grouped per CTA) */
+  LQ2D_OPT_SWEEP_STEPS = 8    /* 1, 2 or 4: time steps each lane carries in the n = 4 FP32 sweeps
+                                  (a CTA then holds threads/8 * steps time steps); the schedules
+                                  compiled are (threads, steps) = (32, 4), (64, 4), (64, 2),
+                                  (128, 2), (32, 2), (64, 1), and any other pair runs as (64, 4).
+                                  Default 4; lq2d_autotune picks the pair by timing.  No effect
+                                  on FP64 sweeps or other n */
 };
 
 /* Statistics of the last solve on a handle. */
@@ -90,7 +96,7 @@ typedef struct lq2d_stats {
   int status;              /* status returned by the solve */
   int sweep_launches;      /* timed sweep launches (timing option) */
   int delta_launches;      /* timed Delta-apply launches (timing option, 2 kernels each) */
-  int pad;
+  int sweep_steps;         /* time steps per lane of the current mode's sweeps (n = 4 FP32), else 1 */
   double rel_residual;     /* ||r||_2 / ||r_delta||_2 of the recurrence residual at exit */
   double rel_kkt_residual; /* ||KKT residual of (x, u, delta)||_2 / ||r_delta||_2 */
   double kkt_inf;          /* max |A~x + B~u + omega~| */
@@ -241,10 +247,12 @@ int lq2d_solve_multi_device(lq2d_problem *h, int nrhs, const void *d_x0s, double
                             int max_iter, void *d_x, void *d_u, void *d_costate, int *iterations,
                             double *rel_residuals, void *stream);
 
-/* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS) for this problem's shape
- * and the handle's current precision mode by timing: runs D_S (S outer x L
+/* Chooses the sweep tile (LQ2D_OPT_SWEEP_THREADS, and for the n = 4 FP32
+ * sweeps also LQ2D_OPT_SWEEP_STEPS) for this problem's shape and the
+ * handle's current precision mode by timing: runs D_S (S outer x L
  * inner sweeps, Algorithm 2) once as warm-up and then `reps` times with each
- * candidate width (32, 64, 128, 256), with CUDA events on `stream`, and keeps
+ * candidate width (32, 64, 128, 256; for n = 4 in FP32 each compiled
+ * (width, steps) schedule), with CUDA events on `stream`, and keeps
  * the fastest for later solves of this precision mode (FP64 and FP32 sweeps
  * keep separate choices).  The problem's right-hand side is the input; the
  * handle's solution buffers are not touched.
@@ -303,6 +311,38 @@ int lq2d_batch_create(lq2d_batch **out, int count, lq2d_problem *const *problems
 int lq2d_batch_solve(lq2d_batch *b, double tol, int outer_S, int inner_L, int max_iter,
                      int *iterations, double *rel_kkt_residuals, int *statuses, void *stream);
 void lq2d_batch_destroy(lq2d_batch *b);
+
+/* Options of a batch (lq2d_batch_set_option / lq2d_batch_get_option).
+ * When every problem has n = 4, precision mode 0 and the NBJM
+ * preconditioner, and S*L <= 14, the loop of Algorithm 1 runs persistently
+ * for the whole batch: one conditional loop whose body is one launch of the
+ * Delta product (two kernels) and one launch per NBJM sweep for all
+ * problems, each a single wave of CTAs sized by occupancy that pull
+ * (problem, node-time block) or (problem, column pair, time tile) units from
+ * a device work queue; problems that have stopped skip their units.  Each
+ * problem's arithmetic and reductions are those of its single solve with the
+ * same sweep width, so the results are equal bit for bit.  Other batches
+ * keep one chain per problem in the graph. */
+enum {
+  LQ2D_BATCH_PERSISTENT = 1,      /* 1 (default): use the persistent loop when the problems allow it; 0: never */
+  LQ2D_BATCH_THREADS = 2,         /* CTA width of its sweeps: 32, 64 (default) or 128 */
+  LQ2D_BATCH_USES_PERSISTENT = 3  /* read only: 1 if the last built graph runs the persistent loop */
+};
+/* Setting an option makes the next lq2d_batch_solve rebuild its graph.
+ * Errors: LQ2D_EINVAL for an unknown option or value. */
+int lq2d_batch_set_option(lq2d_batch *b, int option, int value);
+int lq2d_batch_get_option(const lq2d_batch *b, int option, int *value);
+/* Chooses LQ2D_BATCH_THREADS by timing: for each width (32, 64, 128) runs
+ * one D_S application (S outer x L inner sweeps of Algorithm 2, right-hand
+ * sides as input) of every problem through the persistent sweep launches,
+ * once as warm-up and then `reps` times with CUDA events on `stream`, and
+ * keeps the fastest.  threads and ms (per D_S of the whole batch) are
+ * optional outputs.  Errors: LQ2D_EINVAL when the batch cannot run the
+ * persistent loop or for bad S, L, reps; LQ2D_ECUDA.  Leaves every
+ * problem's solver state reset; returns after the work on `stream` is
+ * complete. */
+int lq2d_batch_autotune(lq2d_batch *b, int outer_S, int inner_L, int reps, int *threads, double *ms,
+                        void *stream);
 /* Copies the solution of the problem's last solve (x, u, costate, layouts as
  * in lq2d_solve_device) into device buffers; any pointer may be NULL. */
 int lq2d_get_solution_device(lq2d_problem *h, void *d_x, void *d_u, void *d_costate, void *stream);

@@ -133,9 +133,12 @@ __device__ inline double warp_max(double v) {
 // last-block reduction over the per-block partials.  Every thread of the
 // block must call it.  Returns true in thread 0 of the last block to arrive,
 // with the grid totals in *out0 / *out1 (partials summed in block order).
+// bid / nblocks: this block's index among the blocks that share `counter`
+// and `partials` (the launch's blocks, or one problem's work units inside a
+// batched launch).
 template <bool SECOND_IS_MAX>
-__device__ inline bool grid_reduce2(double v0, double v1, double* partials, unsigned int* counter,
-                                    double* out0, double* out1) {
+__device__ inline bool grid_reduce2_at(double v0, double v1, double* partials, unsigned int* counter,
+                                       double* out0, double* out1, unsigned bid, unsigned nblocks) {
   __shared__ double s0[32];
   __shared__ double s1[32];
   __shared__ bool is_last;
@@ -147,11 +150,11 @@ __device__ inline bool grid_reduce2(double v0, double v1, double* partials, unsi
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < nw; ++w) { a += s0[w]; b = SECOND_IS_MAX ? fmax(b, s1[w]) : b + s1[w]; }
-    partials[2 * blockIdx.x] = a;
-    partials[2 * blockIdx.x + 1] = b;
+    partials[2 * bid] = a;
+    partials[2 * bid + 1] = b;
     __threadfence();
     unsigned int prev = atomicAdd(counter, 1u);
-    is_last = (prev == gridDim.x - 1);
+    is_last = (prev == nblocks - 1);
   }
   __syncthreads();
   if (!is_last) return false;
@@ -159,7 +162,7 @@ __device__ inline bool grid_reduce2(double v0, double v1, double* partials, unsi
   // The last block sums the partials with a fixed assignment and a fixed
   // tree, so the result does not depend on the order of arrival.
   double a = 0.0, b = 0.0;
-  for (unsigned int blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) {
+  for (unsigned int blk = threadIdx.x; blk < nblocks; blk += blockDim.x) {
     const volatile double* vp = partials;
     a += vp[2 * blk];
     b = SECOND_IS_MAX ? fmax(b, vp[2 * blk + 1]) : b + vp[2 * blk + 1];
@@ -176,6 +179,12 @@ __device__ inline bool grid_reduce2(double v0, double v1, double* partials, unsi
   *out1 = tb;
   *counter = 0u;
   return true;
+}
+
+template <bool SECOND_IS_MAX>
+__device__ inline bool grid_reduce2(double v0, double v1, double* partials, unsigned int* counter,
+                                    double* out0, double* out1) {
+  return grid_reduce2_at<SECOND_IS_MAX>(v0, v1, partials, counter, out0, out1, blockIdx.x, gridDim.x);
 }
 
 }  // namespace lq2d

@@ -39,7 +39,16 @@ struct PrecData {
   const VT* AQ;       // [NN][5][n][n]
   const VT* QAt;      // [NN][5][n][n]
   const VT* Qm;       // [NN][n][n]
+  // FP32, n = 4: records of Phi_bar_{v,0} = blkdiag(Q^-1) in the layout of
+  // fac ([V][K] records, F = N = 0, D^-1 = blkdiag(Q, Q)); NULL otherwise
+  const VT* fac_t0;
 };
+
+// Layout of the preconditioner's FP32 iterates (theta, delta^(s) and its
+// output q in the mixed modes): node-major, v[(p*(T+1) + t)*n + k], so that
+// one (node, t) is n contiguous values and a node's time window is one
+// contiguous run.  FP64 vectors use the component planes of common.cuh.
+__host__ __device__ inline long long iter_f32_index(int n, int k, long long pt) { return pt * n + k; }
 
 // Arguments of one NBJM sweep: theta_out = Phi~^-1 tau with
 //   tau = src                           (first sweep of the first outer step)
@@ -47,10 +56,15 @@ struct PrecData {
 //   tau = src + Omega~ theta_in         (later sweeps)
 // and, in the first sweep of a PCG step, the update of Algorithm 1 lines
 // 9-10 fused in front (delta += vartheta d, r -= vartheta y; tau = r).
-// The iterates theta and delta_s are in the sweep precision VT; the PCG
-// vectors r, delta, y, d and the stored r_theta are always double.
+// The iterates theta and delta_s are in the sweep precision VT (FP32 ones
+// node-major, iter_f32_index); the PCG vectors r, delta, y, d are double in
+// component planes, and so is the stored r_theta except in the n = 4 FP32
+// sweeps, which keep it as FP32 in the node-major layout.
 template <typename VT>
 struct SweepArgsT {
+  // the source tau of the first sweep of a later inner step: FP64 r in
+  // component planes, or (src_rtheta != 0, n = 4 FP32 sweeps) the stored
+  // r_theta as FP32 in the iterates' node-major layout
   const double* src;
   double* rtheta_out;
   const VT* delta_s;
@@ -61,6 +75,8 @@ struct SweepArgsT {
   const double* y;
   const double* d;
   double* partials;
+  int src_rtheta;
+  int* fault;  // set when a bounded wait of the sweep ran out (may be NULL)
 };
 using SweepArgs = SweepArgsT<double>;
 
@@ -101,9 +117,10 @@ struct KernelTable {
   void (*sweep)(int variant, int threads, const Grid& g, const PrecData<double>& pd, const SweepArgsT<double>& a,
                 SolverState* st, cudaStream_t s);
   // FP32 sweep of the mixed mode; the OmegaMu variant sets the flexible
-  // beta = q_new'(r_new - r_old) / mu_old = -vartheta q_new'y / mu_old
-  void (*sweep_f32)(int variant, int threads, const Grid& g, const PrecData<float>& pd, const SweepArgsT<float>& a,
-                    SolverState* st, cudaStream_t s);
+  // beta = q_new'(r_new - r_old) / mu_old = -vartheta q_new'y / mu_old.
+  // steps: time steps per lane of the n = 4 schedule (ignored for other n)
+  void (*sweep_f32)(int variant, int threads, int steps, const Grid& g, const PrecData<float>& pd,
+                    const SweepArgsT<float>& a, SolverState* st, cudaStream_t s);
   // KKT residual pieces and cost of (x, u, delta): out[0] = sum of squared
   // residual entries, out[1] = x'Q~x + u'R~u, out[2] = max |A~x + B~u + omega~|
   void (*kkt)(const Grid& g, const NodeData& nd, const double* x, const double* u, const double* delta,
@@ -113,6 +130,16 @@ struct KernelTable {
 };
 
 const KernelTable* kernel_table(int n);
+
+// The n = 4 FP32 sweep with bulk-copy staging (sweep_bulk.cu): launch with a
+// schedule (threads per CTA, time steps per lane), the schedules compiled,
+// and the shared-memory limits of its kernels.
+void launch_sweep4_f32(int variant, int threads, int steps, const Grid& g, const PrecData<float>& pd,
+                       const SweepArgsT<float>& a, SolverState* st, cudaStream_t s);
+bool sweep4_f32_config_ok(int threads, int steps);
+int sweep4_f32_configs(int (*out)[2], int cap);
+cudaError_t prepare_sweep4_f32();
+constexpr int kSweepSteps = 4;  // default time steps per lane of the n = 4 FP32 sweep
 
 // dimension-generic helpers (kernels_misc.cu)
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,
@@ -141,5 +168,11 @@ void launch_recover_u(const Grid& g, const NodeData& nd, const double* delta, do
 void launch_loop_ctrl(SolverState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_to_f32(const double* src, float* dst, long long count, cudaStream_t s);
 void launch_to_f64(const float* src, double* dst, long long count, cudaStream_t s);
+// an FP32 iterate of the preconditioner (node-major) into an FP64 vector in
+// component planes
+void launch_iter_f32_to_f64(const Grid& g, const float* src, double* dst, cudaStream_t s);
+// records of the t = 0 factor class for the n = 4 FP32 sweeps: F = N = 0,
+// D^-1 = blkdiag(Q of the pair-row's nodes), from the FP32 copy of Q
+void launch_t0_records(const Grid& g, const float* Q32, float* rec, long long fac_rec, cudaStream_t s);
 
 }  // namespace lq2d

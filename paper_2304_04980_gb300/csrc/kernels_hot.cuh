@@ -24,6 +24,15 @@ __device__ __forceinline__ auto ahat_col(const D& nd, int r, int dir) {
   return dir == kSelf ? nd.Aself + (size_t)r * NS * NS : nd.Anb + ((size_t)r * 4 + slot) * NS * NS;
 }
 
+// Element of the preconditioner output q at component k of (node, t) with
+// pt = node*(T+1) + t: component planes in FP64, node-major in FP32 (the
+// layout of the FP32 sweeps' iterates, iter_f32_index).
+template <int NS, typename QT>
+__device__ __forceinline__ long long q_index(const Grid& g, int k, long long pt) {
+  if constexpr (sizeof(QT) == 4) return iter_f32_index(NS, k, pt);
+  else return k * g.Ps + pt;
+}
+
 // ---------------------------------------------------------------------------
 // Delta apply, part 1: z = Q~^-1 A~' dn, one thread per (node, t).
 //   (A~' dn)_t = -dn_t + A_hat' dn_{t+1}   (t < T),   (A~' dn)_T = -dn_T
@@ -35,13 +44,12 @@ __device__ __forceinline__ auto ahat_col(const D& nd, int r, int dir) {
 // replacement (the reliable update of precision mode 2).
 // ---------------------------------------------------------------------------
 template <int NS, typename QT, typename CT, typename DT>
-__global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> nd, const QT* __restrict__ q,
-                                                             const DT* __restrict__ dold,
-                                                             CT* __restrict__ z,
-                                                             const SolverState* __restrict__ st, int use_beta) {
+__device__ __forceinline__ void delta_z_body(const Grid& g, const OpData<CT>& nd, const QT* __restrict__ q,
+                                             const DT* __restrict__ dold, CT* __restrict__ z,
+                                             const SolverState* __restrict__ st, int use_beta, long long bid) {
   if (use_beta == 1 && st->done) return;
   if (use_beta == 2 && (st->done || !st->replace)) return;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = bid * kOpThreads + threadIdx.x;
   if (idx >= g.P) return;
   const int Tp = g.T + 1;
   const int p = (int)(idx / Tp), t = (int)(idx % Tp);
@@ -53,7 +61,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
   CT w[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    DT dv = (DT)q[k * g.Ps + idx];
+    DT dv = (DT)q[q_index<NS, QT>(g, k, idx)];
     if (mix) dv += beta * dold[k * g.Ps + idx];
     w[k] = (CT)(-dv);
   }
@@ -67,7 +75,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
       CT dv[NS];
 #pragma unroll
       for (int c = 0; c < NS; ++c) {
-        DT dd = (DT)q[c * g.Ps + ridx];
+        DT dd = (DT)q[q_index<NS, QT>(g, c, ridx)];
         if (mix) dd += beta * dold[c * g.Ps + ridx];
         dv[c] = (CT)dd;
       }
@@ -87,6 +95,14 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
   }
 }
 
+template <int NS, typename QT, typename CT, typename DT>
+__global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> nd, const QT* __restrict__ q,
+                                                             const DT* __restrict__ dold,
+                                                             CT* __restrict__ z,
+                                                             const SolverState* __restrict__ st, int use_beta) {
+  delta_z_body<NS, QT, CT, DT>(g, nd, q, dold, z, st, use_beta, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Delta apply, part 2: y = A~ z + B~ R~^-1 B~' dn, one thread per (node, t).
 //   y_0 = -z_0,   y_t = A_hat z_{t-1} - z_t + S dn_t   (t >= 1, S = B R^-1 B')
@@ -96,15 +112,14 @@ __global__ void __launch_bounds__(kOpThreads) delta_z_kernel(Grid g, OpData<CT> 
 // replacement (the reliable update of precision mode 2).
 // ---------------------------------------------------------------------------
 template <int NS, bool LOOP, typename QT, typename CT>
-__global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> nd, const CT* __restrict__ z,
-                                                             const QT* __restrict__ q,
-                                                             const double* __restrict__ dold,
-                                                             double* __restrict__ dout, float* __restrict__ dout32,
-                                                             double* __restrict__ y, double* __restrict__ partials,
-                                                             SolverState* st) {
+__device__ __forceinline__ void delta_y_body(const Grid& g, const OpData<CT>& nd, const CT* __restrict__ z,
+                                             const QT* __restrict__ q, const double* __restrict__ dold,
+                                             double* __restrict__ dout, float* __restrict__ dout32,
+                                             double* __restrict__ y, double* __restrict__ partials,
+                                             SolverState* st, long long bid, long long nblocks) {
   if (LOOP && st->done) return;
   if (!LOOP && st != nullptr && (st->done || !st->replace)) return;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = bid * kOpThreads + threadIdx.x;
   double acc = 0.0;
   if (idx < g.P) {
     const int Tp = g.T + 1;
@@ -115,7 +130,7 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> 
     CT yk[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      double dv = (double)q[k * g.Ps + idx];
+      double dv = (double)q[q_index<NS, QT>(g, k, idx)];
       if (LOOP && beta != 0.0) dv += beta * dold[k * g.Ps + idx];
       dn[k] = dv;
       yk[k] = -z[k * g.Ps + idx];
@@ -153,12 +168,23 @@ __global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> 
   }
   if (LOOP) {
     double tot0, tot1;
-    if (grid_reduce2<false>(acc, 0.0, partials, &st->counters[kCntDot], &tot0, &tot1)) {
+    if (grid_reduce2_at<false>(acc, 0.0, partials, &st->counters[kCntDot], &tot0, &tot1, (unsigned)bid,
+                               (unsigned)nblocks)) {
       st->ydot = tot0;
       if (!(tot0 > 0.0) || !isfinite(tot0)) st->done = kBreakdown;
       else st->theta = st->mu / tot0;
     }
   }
+}
+
+template <int NS, bool LOOP, typename QT, typename CT>
+__global__ void __launch_bounds__(kOpThreads) delta_y_kernel(Grid g, OpData<CT> nd, const CT* __restrict__ z,
+                                                             const QT* __restrict__ q,
+                                                             const double* __restrict__ dold,
+                                                             double* __restrict__ dout, float* __restrict__ dout32,
+                                                             double* __restrict__ y, double* __restrict__ partials,
+                                                             SolverState* st) {
+  delta_y_body<NS, LOOP, QT, CT>(g, nd, z, q, dold, dout, dout32, y, partials, st, blockIdx.x, gridDim.x);
 }
 
 }  // namespace hot
@@ -341,13 +367,28 @@ cudaError_t prepare_sweeps_t() {
 
 template <int NS>
 cudaError_t prepare_sweeps() {
-  cudaError_t e[8] = {prepare_sweeps_t<NS, double, 32>(),  prepare_sweeps_t<NS, float, 32>(),
-                      prepare_sweeps_t<NS, double, 64>(),  prepare_sweeps_t<NS, float, 64>(),
-                      prepare_sweeps_t<NS, double, 128>(), prepare_sweeps_t<NS, float, 128>(),
-                      prepare_sweeps_t<NS, double, 256>(), prepare_sweeps_t<NS, float, 256>()};
+  cudaError_t e[4] = {prepare_sweeps_t<NS, double, 32>(), prepare_sweeps_t<NS, double, 64>(),
+                      prepare_sweeps_t<NS, double, 128>(), prepare_sweeps_t<NS, double, 256>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
-  return cudaSuccess;
+  if constexpr (NS == 4) {
+    // n = 4 runs its FP32 sweeps with bulk-copy staging (sweep_bulk.cu)
+    return prepare_sweep4_f32();
+  } else {
+    cudaError_t f[4] = {prepare_sweeps_t<NS, float, 32>(), prepare_sweeps_t<NS, float, 64>(),
+                        prepare_sweeps_t<NS, float, 128>(), prepare_sweeps_t<NS, float, 256>()};
+    for (cudaError_t x : f)
+      if (x != cudaSuccess) return x;
+    return cudaSuccess;
+  }
+}
+
+// FP32 sweep: the bulk-copy kernels for n = 4, the tiled kernel otherwise.
+template <int NS>
+void launch_sweep_f32(int variant, int threads, int steps, const Grid& g, const PrecData<float>& pd,
+                      const SweepArgsT<float>& a, SolverState* st, cudaStream_t s) {
+  if constexpr (NS == 4) launch_sweep4_f32(variant, threads, steps, g, pd, a, st, s);
+  else launch_sweep<NS, float>(variant, threads, g, pd, a, st, s);
 }
 
 template <int NS>
@@ -364,7 +405,7 @@ const KernelTable* make_table() {
                                 &launch_delta_z<NS, float, float, float>,
                                 &launch_delta_y<NS, double, double>, &launch_delta_y<NS, float, double>,
                                 &launch_delta_y_impl<NS, float, float>,
-                                &launch_sweep<NS, double>,   &launch_sweep<NS, float>,
+                                &launch_sweep<NS, double>,   &launch_sweep_f32<NS>,
                                 &launch_kkt<NS>, &prepare_sweeps<NS>};
   return &t;
 }

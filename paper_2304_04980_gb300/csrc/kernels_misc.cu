@@ -116,7 +116,7 @@ __global__ void nbjm_diff_kernel(Grid g, const VT* __restrict__ a, const VT* __r
   double mx = 0.0;
   if (idx < g.P)
     for (int k = 0; k < g.n; ++k) {
-      const long long e = k * g.Ps + idx;
+      const long long e = sizeof(VT) == 4 ? iter_f32_index(g.n, k, idx) : k * g.Ps + idx;
       const double dv = (double)a[e] - (b != nullptr ? (double)b[e] : 0.0);
       mx = fmax(mx, fabs(dv));
     }
@@ -283,6 +283,36 @@ __global__ void to_f64_kernel(const float* __restrict__ src, double* __restrict_
   if (i < count) dst[i] = (double)src[i];
 }
 
+// FP32 iterate (node-major) -> FP64 component planes, one thread per (node, t)
+__global__ void iter_f32_to_f64_kernel(Grid g, const float* __restrict__ src, double* __restrict__ dst) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.P) return;
+  for (int k = 0; k < g.n; ++k) dst[k * g.Ps + idx] = (double)src[iter_f32_index(g.n, k, idx)];
+}
+
+// Records of Phi_bar_{v,0} = blkdiag(Q^-1) for the n = 4 FP32 sweeps, in the
+// record layout of the banded factors ([N2][N1][D^-1][F2][F1][L0^-1] blocks
+// of (2n)^2): the unit factor is the identity (F = N = 0) and D^-1 =
+// blkdiag(Q of node (i, 2v), Q of node (i, 2v+1)); a missing second column
+// (odd N) gets zero rows.  One thread per record entry.
+__global__ void t0_records_kernel(Grid g, const float* __restrict__ Q, float* __restrict__ rec, long long fac_rec) {
+  const int n = g.n, G2 = 2 * n, BS = G2 * G2;
+  const long long total = (long long)g.V * g.K * fac_rec;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const long long vr = e / fac_rec;  // (v, i) record
+  const int within = (int)(e % fac_rec);
+  const int v = (int)(vr / g.K), i = (int)(vr % g.K);
+  float val = 0.f;
+  if (within >= 2 * BS && within < 3 * BS) {
+    const int rc = within - 2 * BS, a = rc / G2, b = rc % G2;
+    const int ja = a / n, jb = b / n;
+    const int j = 2 * v + ja;
+    if (ja == jb && j < g.N) val = Q[((size_t)i * g.N + j) * n * n + (a % n) * n + (b % n)];
+  }
+  rec[e] = val;
+}
+
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -355,6 +385,15 @@ void launch_to_f32(const double* src, float* dst, long long count, cudaStream_t 
 
 void launch_to_f64(const float* src, double* dst, long long count, cudaStream_t s) {
   to_f64_kernel<<<blocks_for(count, 256), 256, 0, s>>>(src, dst, count);
+}
+
+void launch_iter_f32_to_f64(const Grid& g, const float* src, double* dst, cudaStream_t s) {
+  iter_f32_to_f64_kernel<<<blocks_for(g.P, 256), 256, 0, s>>>(g, src, dst);
+}
+
+void launch_t0_records(const Grid& g, const float* Q32, float* rec, long long fac_rec, cudaStream_t s) {
+  const long long total = (long long)g.V * g.K * fac_rec;
+  t0_records_kernel<<<blocks_for(total, 256), 256, 0, s>>>(g, Q32, rec, fac_rec);
 }
 
 }  // namespace lq2d

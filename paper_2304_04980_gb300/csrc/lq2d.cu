@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/lq2d.h"
+#include "batch.h"
 #include "kernels.h"
 #include "mrhs.h"
 #include "setup.h"
@@ -93,6 +94,8 @@ struct lq2d_problem {
   float* d32 = nullptr;      // FP32 copy of the direction d (mode 2)
   int precond_kind = 0;      // 0: NBJM (Algorithm 2), 1: none (plain CG)
   int sweep_threads[2] = {kSweepThreads, kSweepThreads};  // CTA width of the FP64 / FP32 sweeps (32..256)
+  int sweep_steps = kSweepSteps;  // time steps per lane of the n = 4 FP32 sweeps
+  int* fault = nullptr;           // device word set when a bounded wait inside a sweep ran out
   int kappa = 0;             // record the PCG coefficients and estimate the condition number
   double* hist = nullptr;    // device: vartheta_j, beta_j pairs
   std::vector<double> h_hist;
@@ -126,6 +129,16 @@ struct lq2d_batch {
   double tol = 0.0;
   int S = 0, L = 0, max_iter = -1;
   std::vector<int> built_modes;
+  // persistent batched loop (problems with n = 4 in FP64 with the NBJM
+  // preconditioner): one launch per kernel of a PCG step for all problems
+  int persistent = 1;              // option: use it when the problems allow it
+  int threads = kSweepThreads;     // CTA width of its sweeps (32, 64 or 128)
+  bool built_persistent = false;   // the current graph is the persistent one
+  BatchPlan plan{};                // device arrays, inside plan_mem
+  void* plan_mem = nullptr;
+  size_t plan_bytes = 0;
+  std::vector<int> variants;       // [2 S L]: loop-step sweeps, then a plain D_S
+  unsigned* h_heads = nullptr;     // pinned: the queue heads and the pass counter
 };
 
 namespace {
@@ -251,6 +264,7 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   h->bnorm = misc;
   h->kkt_out = misc + 8;
   h->setup_status = reinterpret_cast<int*>(misc + 16);
+  h->fault = h->setup_status + 1;
   h->st = reinterpret_cast<SolverState*>(misc + 24);
   static_assert(sizeof(SolverState) <= 40 * sizeof(double), "state slot");
 #undef ALLOC
@@ -270,8 +284,8 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
 
 // Element counts of the FP32 operand copies: the preconditioner's factors,
 // Omega~, AQ, QAt, Q, then the Delta product's A, E/F/G/H, Q^-1, Q_T^-1,
-// B R^-1 B'.
-constexpr int kF32Arrays = 10;
+// B R^-1 B', and (n = 4) the records of the t = 0 factor class.
+constexpr int kF32Arrays = 11;
 void prec_counts(const lq2d_problem* h, long long c[kF32Arrays]) {
   const Grid& g = h->g;
   const long long nn = (long long)g.n * g.n;
@@ -285,20 +299,25 @@ void prec_counts(const lq2d_problem* h, long long c[kF32Arrays]) {
   c[7] = c[5];
   c[8] = c[5];
   c[9] = c[5];
+  c[10] = g.n == 4 ? (long long)g.V * g.K * h->nd.fac_rec : 0;
 }
 
 // FP32 copies of the operands for the mixed modes.
 void convert_prec_f32(lq2d_problem* h, cudaStream_t s) {
   long long c[kF32Arrays];
   prec_counts(h, c);
-  const double* src[kF32Arrays] = {h->sb.fac, h->sb.Om, h->sb.AQ, h->sb.QAt, h->sb.Qm,
-                                   h->sb.Aself, h->sb.Anb, h->sb.Qi, h->sb.QTi, h->sb.Sb};
+  const double* src[kF32Arrays - 1] = {h->sb.fac, h->sb.Om, h->sb.AQ, h->sb.QAt, h->sb.Qm,
+                                       h->sb.Aself, h->sb.Anb, h->sb.Qi, h->sb.QTi, h->sb.Sb};
   float* dst = h->f32_buf;
-  for (int a = 0; a < kF32Arrays; ++a) {
+  for (int a = 0; a < kF32Arrays - 1; ++a) {
     launch_to_f32(src[a], dst, c[a], s);
     dst += c[a];
   }
-  h->launches += kF32Arrays;
+  h->launches += kF32Arrays - 1;
+  if (c[kF32Arrays - 1] > 0) {
+    launch_t0_records(h->g, h->pd32.Qm, const_cast<float*>(h->pd32.fac_t0), h->nd.fac_rec, s);
+    h->launches += 1;
+  }
 }
 
 // Setup on `s`: inverses, splitting blocks, factors, right-hand side and its
@@ -355,14 +374,21 @@ int create_common(lq2d_problem** out, int K, int N, int T, int n, int m, const d
   return LQ2D_OK;
 }
 
-// One preconditioner application q = D_S r_in (Algorithm 2, S x L sweeps
-// from zero starts).  fuse_update: the first sweep also performs the update
-// and stop test of Algorithm 1; mu: the last sweep reduces mu = q' r.  Returns the buffer
-// holding q (thB, since S*L is even); its elements are double in FP64 mode
-// and float in the mixed mode.
+// The S x L sweeps of one preconditioner application q = D_S r_in
+// (Algorithm 2 from zero starts): each sweep's variant and arguments, in
+// launch order.  fuse_update: the first sweep also performs the update and
+// stop test of Algorithm 1; mu: the last sweep reduces mu = q' r.  The
+// iterates alternate between thA and thB, so q ends in thB (S*L is even);
+// its elements are double in FP64 mode and float in the mixed modes.
 template <typename VT>
-const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
-                              const double* r_in, cudaStream_t s, bool timing) {
+struct SweepPlanEntry {
+  int variant;
+  SweepArgsT<VT> a;
+};
+template <typename VT>
+std::vector<SweepPlanEntry<VT>> precond_plan(lq2d_problem* h, int S, int L, bool fuse_update, bool mu,
+                                             const double* r_in) {
+  std::vector<SweepPlanEntry<VT>> plan;
   VT* bufs[2] = {reinterpret_cast<VT*>(h->thA), reinterpret_cast<VT*>(h->thB)};
   int out_i = 0;
   const VT* prev = nullptr;
@@ -372,6 +398,7 @@ const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, b
       a.partials = h->partials;
       a.theta_out = bufs[out_i];
       a.y = h->y;
+      a.fault = h->fault;
       int variant;
       if (l == 0 && so == 0) {
         variant = fuse_update ? kSweepUpdate : kSweepPlain;
@@ -387,30 +414,43 @@ const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, b
       } else {
         variant = (mu && so == S - 1 && l == L - 1) ? kSweepOmegaMu : kSweepOmega;
         a.src = so == 0 ? r_in : h->rth;
+        a.src_rtheta = so == 0 ? 0 : 1;
         a.theta_in = prev;
         a.r = const_cast<double*>(r_in);
       }
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (timing) {
-        const size_t k = h->ev_pool.size();
-        h->ev_pool.resize(k + 2);
-        cudaEventCreate(&h->ev_pool[k]);
-        cudaEventCreate(&h->ev_pool[k + 1]);
-        e0 = h->ev_pool[k];
-        e1 = h->ev_pool[k + 1];
-        cudaEventRecord(e0, s);
-      }
-      if constexpr (sizeof(VT) == 4)
-        h->kt->sweep_f32(variant, h->sweep_threads[1], h->g, h->pd32, a, st, s);
-      else
-        h->kt->sweep(variant, h->sweep_threads[0], h->g, h->pd64, a, st, s);
-      h->launches += 1;
-      if (timing) cudaEventRecord(e1, s);
+      plan.push_back({variant, a});
       prev = bufs[out_i];
       out_i ^= 1;
     }
   }
-  return prev;
+  return plan;
+}
+
+// One preconditioner application (the plan above, launched on `s`).
+// Returns the buffer holding q.
+template <typename VT>
+const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
+                              const double* r_in, cudaStream_t s, bool timing) {
+  const std::vector<SweepPlanEntry<VT>> plan = precond_plan<VT>(h, S, L, fuse_update, mu, r_in);
+  for (const SweepPlanEntry<VT>& e : plan) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timing) {
+      const size_t k = h->ev_pool.size();
+      h->ev_pool.resize(k + 2);
+      cudaEventCreate(&h->ev_pool[k]);
+      cudaEventCreate(&h->ev_pool[k + 1]);
+      e0 = h->ev_pool[k];
+      e1 = h->ev_pool[k + 1];
+      cudaEventRecord(e0, s);
+    }
+    if constexpr (sizeof(VT) == 4)
+      h->kt->sweep_f32(e.variant, h->sweep_threads[1], h->sweep_steps, h->g, h->pd32, e.a, st, s);
+    else
+      h->kt->sweep(e.variant, h->sweep_threads[0], h->g, h->pd64, e.a, st, s);
+    h->launches += 1;
+    if (timing) cudaEventRecord(e1, s);
+  }
+  return plan.back().a.theta_out;
 }
 
 const void* enqueue_precond(lq2d_problem* h, int S, int L, bool fuse_update, bool mu, SolverState* st,
@@ -824,6 +864,7 @@ void enqueue_nbjm_outer(lq2d_problem* h, int L, int step, cudaStream_t s) {
     a.theta_out = B[others[l & 1]];
     a.y = h->y;
     a.r = h->rhs;
+    a.fault = h->fault;
     int variant;
     if (l == 0 && cur < 0) {
       variant = kSweepPlain;
@@ -837,10 +878,11 @@ void enqueue_nbjm_outer(lq2d_problem* h, int L, int step, cudaStream_t s) {
     } else {
       variant = kSweepOmega;
       a.src = cur < 0 ? h->rhs : h->rth;
+      a.src_rtheta = cur < 0 ? 0 : 1;
       a.theta_in = prev;
     }
     if constexpr (sizeof(VT) == 4)
-      h->kt->sweep_f32(variant, h->sweep_threads[1], h->g, h->pd32, a, h->st, s);
+      h->kt->sweep_f32(variant, h->sweep_threads[1], h->sweep_steps, h->g, h->pd32, a, h->st, s);
     else
       h->kt->sweep(variant, h->sweep_threads[0], h->g, h->pd64, a, h->st, s);
     prev = B[others[l & 1]];
@@ -889,7 +931,7 @@ int solve_nbjm_impl(lq2d_problem* h, double eps, int L, int max_outer, double* d
   const int buf = nbjm_buffer_after(steps, L);
   double* B64[3] = {h->thA, h->thB, h->z};
   if (buf >= 0) {
-    if (f32) launch_to_f64(reinterpret_cast<const float*>(B64[buf]), h->delta, (long long)g.Ps * g.n, s);
+    if (f32) launch_iter_f32_to_f64(g, reinterpret_cast<const float*>(B64[buf]), h->delta, s);
     else LQ_CUDA(cudaMemcpyAsync(h->delta, B64[buf], (size_t)g.Ps * g.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
     LQ_CUDA(cudaMemsetAsync(h->delta, 0, (size_t)g.Ps * g.n * sizeof(double), s));
@@ -950,6 +992,135 @@ int batch_mode_key(const lq2d_problem* h) {
   return ((current_threads(h) * 4 + h->precision) * 4 + h->precond_kind) * 4 + h->stop_mode;
 }
 
+// The persistent batched loop serves FP64 NBJM problems with n = 4, S x L
+// sweeps that fit the queue heads.
+bool batch_persistent_ok(const lq2d_batch* b, int S, int L) {
+  if (!b->persistent || S * L + 2 > kBatchHeads) return false;
+  for (const lq2d_problem* h : b->probs)
+    if (h->g.n != 4 || h->precision != 0 || h->precond_kind != 0) return false;
+  return true;
+}
+
+// Uploads the batch plan (problem descriptors, unit offsets, the arguments
+// of every sweep of a loop step and of a plain D_S application) for the
+// batch's CTA width; sets the persistent grid sizes.
+int batch_plan_upload(lq2d_batch* b, int S, int L, cudaStream_t s) {
+  const int np = (int)b->probs.size();
+  const int SL = S * L;
+  std::vector<BatchProblem> probs(np);
+  std::vector<int> soff(np + 1, 0);
+  std::vector<long long> ooff(np + 1, 0);
+  std::vector<SweepArgsT<double>> args((size_t)2 * SL * np);
+  b->variants.assign(2 * SL, 0);
+  for (int i = 0; i < np; ++i) {
+    lq2d_problem* h = b->probs[i];
+    BatchProblem& P = probs[i];
+    P.g = h->g;
+    P.op = h->op64;
+    P.pd = h->pd64;
+    P.st = h->st;
+    P.partials = h->partials;
+    P.q = h->thB;
+    P.d = h->d;
+    P.y = h->y;
+    P.z = h->z;
+    soff[i + 1] = soff[i] + batch_sweep_units(h->g, b->threads);
+    ooff[i + 1] = ooff[i] + (h->g.P + kOpThreads - 1) / kOpThreads;
+    const std::vector<SweepPlanEntry<double>> loop = precond_plan<double>(h, S, L, true, true, h->r);
+    const std::vector<SweepPlanEntry<double>> plain = precond_plan<double>(h, S, L, false, false, h->rhs);
+    for (int k = 0; k < SL; ++k) {
+      args[(size_t)k * np + i] = loop[k].a;
+      args[(size_t)(SL + k) * np + i] = plain[k].a;
+      b->variants[k] = loop[k].variant;
+      b->variants[SL + k] = plain[k].variant;
+    }
+  }
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t o_probs = 0, o_soff = up(np * sizeof(BatchProblem)), o_ooff = o_soff + up((np + 1) * sizeof(int)),
+               o_args = o_ooff + up((np + 1) * sizeof(long long)),
+               o_heads = o_args + up(args.size() * sizeof(SweepArgsT<double>)),
+               total = o_heads + up((kBatchHeads + 1) * sizeof(unsigned));
+  if (total > b->plan_bytes) {
+    if (b->plan_mem) cudaFree(b->plan_mem);
+    b->plan_mem = nullptr;
+    b->plan_bytes = 0;
+    cudaError_t e = cudaMalloc(&b->plan_mem, total);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LQ2D_ENOMEM : LQ2D_ECUDA, cudaGetErrorString(e));
+    b->plan_bytes = total;
+  }
+  char* base = static_cast<char*>(b->plan_mem);
+  BatchPlan& pl = b->plan;
+  pl.probs = reinterpret_cast<BatchProblem*>(base + o_probs);
+  pl.sweep_off = reinterpret_cast<int*>(base + o_soff);
+  pl.op_off = reinterpret_cast<long long*>(base + o_ooff);
+  pl.args = reinterpret_cast<SweepArgsT<double>*>(base + o_args);
+  pl.heads = reinterpret_cast<unsigned*>(base + o_heads);
+  pl.nprob = np;
+  pl.threads = b->threads;
+  LQ_CUDA(cudaMemcpyAsync(pl.probs, probs.data(), np * sizeof(BatchProblem), cudaMemcpyHostToDevice, s));
+  LQ_CUDA(cudaMemcpyAsync(pl.sweep_off, soff.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  LQ_CUDA(cudaMemcpyAsync(pl.op_off, ooff.data(), (np + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+  LQ_CUDA(cudaMemcpyAsync(pl.args, args.data(), args.size() * sizeof(SweepArgsT<double>), cudaMemcpyHostToDevice, s));
+  LQ_CUDA(cudaMemsetAsync(pl.heads, 0, (kBatchHeads + 1) * sizeof(unsigned), s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  LQ_CUDA(batch_grid_sizes(pl));
+  return LQ2D_OK;
+}
+
+// The persistent graph: every problem's initial part (independent), one
+// conditional while node whose body is the batched step (Delta product, the
+// S x L sweeps, loop control), then every problem's recovery.
+int batch_build_persistent(lq2d_batch* b, double tol, int S, int L, int max_iter) {
+  int rc = batch_plan_upload(b, S, L, b->cap);
+  if (rc) return rc;
+  cudaGraph_t root = b->graph;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  std::vector<cudaGraphNode_t> tails;
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t captured = nullptr;
+  LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, root, nullptr, nullptr, 0, mode));
+  LQ_CUDA(cudaMemsetAsync(b->plan.heads, 0, (kBatchHeads + 1) * sizeof(unsigned), b->cap));
+  LQ_CUDA(cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+  tails.insert(tails.end(), deps, deps + ndeps);
+  LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+  for (lq2d_problem* h : b->probs) {
+    LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, root, nullptr, nullptr, 0, mode));
+    const long long before = h->launches;
+    enqueue_solve_init(h, tol, S, L, max_iter, b->cap);
+    h->launches = before;
+    LQ_CUDA(cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+    tails.insert(tails.end(), deps, deps + ndeps);
+    LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+  }
+  cudaGraphConditionalHandle hc;
+  LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, root, 1u, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_storage, 0, sizeof(cp_storage));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  LQ_CUDA(cudaGraphAddNode(&cnode, root, tails.data(), nullptr, tails.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const int SL = S * L;
+  LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, mode));
+  batch_enqueue_delta(b->plan, 0, b->cap);
+  for (int k = 0; k < SL; ++k) batch_enqueue_sweep(b->plan, b->variants[k], k, 2 + k, b->cap);
+  batch_enqueue_loop_ctrl(b->plan, hc, b->cap);
+  LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+  for (size_t i = 0; i < b->probs.size(); ++i) {
+    LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, root, &cnode, nullptr, 1, mode));
+    enqueue_solve_finish(b->probs[i], b->results + i * kBatchSlot, b->cap);
+    LQ_CUDA(cudaStreamEndCapture(b->cap, &captured));
+  }
+  b->built_persistent = true;
+  return LQ2D_OK;
+}
+
 int batch_build(lq2d_batch* b, double tol, int S, int L, int max_iter) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -959,8 +1130,13 @@ int batch_build(lq2d_batch* b, double tol, int S, int L, int max_iter) {
   cudaGraph_t root;
   LQ_CUDA(cudaGraphCreate(&root, 0));
   b->graph = root;
+  b->built_persistent = false;
+  if (batch_persistent_ok(b, S, L)) {
+    int rc = batch_build_persistent(b, tol, S, L, max_iter);
+    if (rc) return rc;
+  }
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
-  for (size_t i = 0; i < b->probs.size(); ++i) {
+  for (size_t i = 0; !b->built_persistent && i < b->probs.size(); ++i) {
     lq2d_problem* h = b->probs[i];
     // initial part, appended to the root graph with no dependency
     LQ_CUDA(cudaStreamBeginCaptureToGraph(b->cap, root, nullptr, nullptr, 0, mode));
@@ -1041,6 +1217,8 @@ int ensure_f32(lq2d_problem* h) {
     h->op32.QTi = p;
     p += c[8];
     h->op32.Sb = p;
+    p += c[9];
+    h->pd32.fac_t0 = c[10] > 0 ? p : nullptr;
     h->pd32.fac_rec = h->nd.fac_rec;
     h->pd32.fac_vc = h->nd.fac_vc;
     convert_prec_f32(h, nullptr);
@@ -1433,14 +1611,21 @@ int lq2d_apply_precond_device(lq2d_problem* h, int S, int L, const void* d_r, vo
   const void* q = enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
   const double* qd = static_cast<const double*>(q);
   if (h->precision >= 1) {
-    // widen the FP32 result into thA (free after the sweeps) before the layout change
-    launch_to_f64(static_cast<const float*>(q), h->thA, (long long)g.Ps * g.n, s);
+    // widen the FP32 result (node-major) into thA (free after the sweeps) in
+    // component planes, before the layout change
+    launch_iter_f32_to_f64(g, static_cast<const float*>(q), h->thA, s);
     h->launches += 1;
     qd = h->thA;
   }
   launch_to_api(qd, static_cast<double*>(d_q), g.NN, g.T + 1, g.n, g.Ps, s);
+  int fault = 0;
+  LQ_CUDA(cudaMemcpyAsync(&fault, h->fault, sizeof(int), cudaMemcpyDeviceToHost, s));
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
+  if (fault) {
+    LQ_CUDA(cudaMemset(h->fault, 0, sizeof(int)));
+    return fail(LQ2D_ETIMEOUT, "a bounded wait inside a preconditioner sweep ran out");
+  }
   return LQ2D_OK;
 }
 
@@ -1496,12 +1681,19 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
     cudaEventDestroy(e0);
     return fail(LQ2D_ECUDA, "cudaEventCreate failed");
   }
-  const int cand[4] = {32, 64, 128, 256};
+  // candidates: CTA widths, and for the n = 4 FP32 sweeps the compiled
+  // (width, time steps per lane) schedules
+  int cand[8][2] = {{32, 1}, {64, 1}, {128, 1}, {256, 1}};
+  int ncand = 4;
+  const bool bulk = slot == 1 && g.n == 4;
+  if (bulk) ncand = sweep4_f32_configs(cand, 8);
+  const int saved_steps = h->sweep_steps;
   double best_ms = 0.0;
-  int best = saved;
+  int best = saved, best_steps = saved_steps;
   cudaError_t err = cudaSuccess;
-  for (int c = 0; c < 4 && err == cudaSuccess; ++c) {
-    h->sweep_threads[slot] = cand[c];
+  for (int c = 0; c < ncand && err == cudaSuccess; ++c) {
+    h->sweep_threads[slot] = cand[c][0];
+    if (bulk) h->sweep_steps = cand[c][1];
     enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);  // warm-up
     cudaEventRecord(e0, s);
     for (int r = 0; r < reps; ++r) enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
@@ -1512,7 +1704,8 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
     const double per = (double)t / reps;
     if (err == cudaSuccess && (c == 0 || per < best_ms)) {
       best_ms = per;
-      best = cand[c];
+      best = cand[c][0];
+      best_steps = bulk ? cand[c][1] : saved_steps;
     }
   }
   cudaEventDestroy(e0);
@@ -1520,9 +1713,11 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
   if (err == cudaSuccess) err = cudaGetLastError();
   if (err != cudaSuccess) {
     h->sweep_threads[slot] = saved;
+    h->sweep_steps = saved_steps;
     return fail(LQ2D_ECUDA, cudaGetErrorString(err));
   }
   h->sweep_threads[slot] = best;
+  h->sweep_steps = best_steps;
   if (threads) *threads = best;
   if (ms) *ms = best_ms;
   return LQ2D_OK;
@@ -1546,6 +1741,8 @@ int lq2d_batch_create(lq2d_batch** out, int count, lq2d_problem* const* problems
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->results, (size_t)count * kBatchSlot * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_results, (size_t)count * kBatchSlot * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_heads, (kBatchHeads + 1) * sizeof(unsigned));
+  if (e == cudaSuccess) e = batch_prepare();
   if (e != cudaSuccess) {
     lq2d_batch_destroy(b);
     return fail(e == cudaErrorMemoryAllocation ? LQ2D_ENOMEM : LQ2D_ECUDA, cudaGetErrorString(e));
@@ -1573,8 +1770,11 @@ int lq2d_batch_solve(lq2d_batch* b, double tol, int S, int L, int max_iter, int*
   const size_t count = b->probs.size();
   LQ_CUDA(cudaGraphLaunch(b->exec, s));
   LQ_CUDA(cudaMemcpyAsync(b->h_results, b->results, count * kBatchSlot * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (b->built_persistent)
+    LQ_CUDA(cudaMemcpyAsync(b->h_heads, b->plan.heads, (kBatchHeads + 1) * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   LQ_CUDA(cudaStreamSynchronize(s));
   LQ_CUDA(cudaGetLastError());
+  const long long passes = b->built_persistent ? (long long)b->h_heads[kBatchHeads] : 0;
   int worst = LQ2D_OK;
   for (size_t i = 0; i < count; ++i) {
     lq2d_problem* h = b->probs[i];
@@ -1600,7 +1800,12 @@ int lq2d_batch_solve(lq2d_batch* b, double tol, int S, int L, int max_iter, int*
     h->stats.status = status;
     h->stats.body_executions = hs.body_count;
     const int sweeps = sweeps_per_step(h, S, L);
-    h->launches += (2 + sweeps) + 3 + (long long)hs.body_count * (2 + sweeps + 1);
+    if (b->built_persistent) {
+      // the loop's launches serve every problem; they are counted once, on the first
+      h->launches += (2 + sweeps) + 3 + (i == 0 ? passes * (2 + sweeps + 1) : 0);
+    } else {
+      h->launches += (2 + sweeps) + 3 + (long long)hs.body_count * (2 + sweeps + 1);
+    }
     if (iterations) iterations[i] = hs.iter;
     if (rel_kkt) rel_kkt[i] = rel;
     if (statuses) statuses[i] = status;
@@ -1616,8 +1821,101 @@ void lq2d_batch_destroy(lq2d_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->results) cudaFree(b->results);
   if (b->h_results) cudaFreeHost(b->h_results);
+  if (b->h_heads) cudaFreeHost(b->h_heads);
+  if (b->plan_mem) cudaFree(b->plan_mem);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
+}
+
+int lq2d_batch_set_option(lq2d_batch* b, int option, int value) {
+  if (!b) return fail(LQ2D_EINVAL, "batch is NULL");
+  switch (option) {
+    case LQ2D_BATCH_PERSISTENT:
+      if (value != 0 && value != 1) return fail(LQ2D_EINVAL, "persistent must be 0 or 1");
+      b->persistent = value;
+      break;
+    case LQ2D_BATCH_THREADS:
+      if (value != 32 && value != 64 && value != 128) return fail(LQ2D_EINVAL, "batch threads must be 32, 64 or 128");
+      b->threads = value;
+      break;
+    default:
+      return fail(LQ2D_EINVAL, "unknown batch option");
+  }
+  // the next solve rebuilds its graph
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  return LQ2D_OK;
+}
+
+int lq2d_batch_get_option(const lq2d_batch* b, int option, int* value) {
+  if (!b || !value) return fail(LQ2D_EINVAL, "null argument");
+  switch (option) {
+    case LQ2D_BATCH_PERSISTENT: *value = b->persistent; return LQ2D_OK;
+    case LQ2D_BATCH_THREADS: *value = b->threads; return LQ2D_OK;
+    case LQ2D_BATCH_USES_PERSISTENT: *value = b->built_persistent ? 1 : 0; return LQ2D_OK;
+    default: return fail(LQ2D_EINVAL, "unknown batch option");
+  }
+}
+
+int lq2d_batch_autotune(lq2d_batch* b, int S, int L, int reps, int* threads, double* ms, void* stream) {
+  if (!b) return fail(LQ2D_EINVAL, "batch is NULL");
+  if (S < 1 || L < 2 || (L & 1)) return fail(LQ2D_EINVAL, "outer_S >= 1 and even inner_L >= 2 required");
+  if (reps < 1) return fail(LQ2D_EINVAL, "reps must be >= 1");
+  if (!batch_persistent_ok(b, S, L))
+    return fail(LQ2D_EINVAL, "the batch does not run the persistent loop (n = 4, FP64, NBJM problems required)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int SL = S * L;
+  // running states, so that no sweep skips its problem
+  for (lq2d_problem* h : b->probs) {
+    launch_init_state(h->st, 1.0, 1, h->stop_mode, h->bnorm, 0, nullptr, 0, 0.0, s);
+    h->launches += 1;
+  }
+  const int saved = b->threads;
+  const int cand[3] = {32, 64, 128};
+  cudaEvent_t e0, e1;
+  LQ_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(LQ2D_ECUDA, "cudaEventCreate failed");
+  }
+  double best_ms = 0.0;
+  int best = saved, rc = LQ2D_OK;
+  cudaError_t err = cudaSuccess;
+  auto dsr = [&]() {  // one plain D_S application of every problem (r = the right-hand side)
+    cudaMemsetAsync(b->plan.heads, 0, kBatchHeads * sizeof(unsigned), s);
+    for (int k = 0; k < SL; ++k) batch_enqueue_sweep(b->plan, b->variants[SL + k], SL + k, 2 + k, s);
+  };
+  for (int c = 0; c < 3 && err == cudaSuccess && rc == LQ2D_OK; ++c) {
+    b->threads = cand[c];
+    rc = batch_plan_upload(b, S, L, s);
+    if (rc) break;
+    dsr();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) dsr();
+    cudaEventRecord(e1, s);
+    err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    const double per = (double)t / reps;
+    if (err == cudaSuccess && (c == 0 || per < best_ms)) {
+      best_ms = per;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  b->probs[0]->launches += (long long)3 * (reps + 1) * SL;
+  if (rc == LQ2D_OK && err != cudaSuccess) rc = fail(LQ2D_ECUDA, cudaGetErrorString(err));
+  if (rc != LQ2D_OK) best = saved;
+  const int keep = lq2d_batch_set_option(b, LQ2D_BATCH_THREADS, best);
+  if (rc != LQ2D_OK) return rc;
+  if (keep != LQ2D_OK) return keep;
+  if (threads) *threads = best;
+  if (ms) *ms = best_ms;
+  return LQ2D_OK;
 }
 
 int lq2d_get_solution_device(lq2d_problem* h, void* d_x, void* d_u, void* d_costate, void* stream) {
@@ -1664,6 +1962,10 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
         return fail(LQ2D_EINVAL, "sweep threads must be 32, 64, 128 or 256");
       h->sweep_threads[0] = h->sweep_threads[1] = v;
       return LQ2D_OK;
+    case LQ2D_OPT_SWEEP_STEPS:
+      if (v != 1 && v != 2 && v != 4) return fail(LQ2D_EINVAL, "sweep steps must be 1, 2 or 4");
+      h->sweep_steps = v;
+      return LQ2D_OK;
     default:
       return fail(LQ2D_EINVAL, "unknown option");
   }
@@ -1674,6 +1976,7 @@ int lq2d_get_stats(const lq2d_problem* h, lq2d_stats* out) {
   *out = h->stats;
   out->launches_total = h->launches;
   out->sweep_threads = h->sweep_threads[h->precision >= 1 ? 1 : 0];
+  out->sweep_steps = (h->precision >= 1 && h->g.n == 4) ? h->sweep_steps : 1;
   return LQ2D_OK;
 }
 

@@ -156,9 +156,12 @@ constexpr int sweep_min_blocks() {
   return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
 
+// The sweep for work unit `bid` of `nblocks` (one CTA's tile: column pair
+// bid / tiles, time steps from (bid % tiles) * TT); the kernel below runs one
+// unit per CTA, the batched persistent kernel many per CTA.
 template <int NS, int VAR, typename VT, int THR>
-__global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a,
-                                                         SolverState* st) {
+__device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a,
+                                                SolverState* st, int bid, int nblocks) {
   // VT = float is the mixed mode: FP32 factors, blocks and iterates, with
   // the flexible (Polak-Ribiere) ratio for the next direction
   constexpr bool FLEX = sizeof(VT) == 4;
@@ -175,8 +178,8 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   if (st != nullptr && st->done) return;
   const int Tp = g.T + 1;
   const int tiles = (Tp + TT - 1) / TT;
-  const int v = blockIdx.x / tiles;
-  const int t0 = (blockIdx.x % tiles) * TT;
+  const int v = bid / tiles;
+  const int t0 = (bid % tiles) * TT;
   const int j0 = 2 * v;
   const bool two_cols = j0 + 1 < g.N;
   const bool has_last = t0 + TT > g.T;  // the tile holds t = T (class 1)
@@ -193,6 +196,10 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   const int j = j0 + jj;
   const bool node_ok = active && lane_ok && j < g.N;
   const long long kP = (long long)k * g.Ps;
+  // element index of an iterate (theta, delta^(s)) at component kk of
+  // pt = node*(T+1) + t: component planes in FP64, node-major in FP32
+  auto it_idx = [&](int kk, long long pt) -> long long { return FLEX ? pt * NS + kk : kk * g.Ps + pt; };
+  constexpr int VS = FLEX ? NS : 1;  // iterate elements per (node, t) step along a row
   const int cls = (t == g.T) ? 1 : 0;
   const int my_slot = has_last ? cls : 0;  // tiles without t = T stage class 0 only, at slot 0
   const double vth = UPDATE ? st->theta : 0.0;
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       const bool ok = e < HALO_N && tt >= 0 && tt <= g.T && jn >= 0 && jn < g.N;
       // pair-row 0's address; at di = -1 it lies one grid row below the
       // plane's start and is used only from pair-row 1 on
-      h_ptr[sl] = vec + (ok ? kk * g.Ps + (long long)(di * g.N + jn) * Tp + tt : 0);
+      h_ptr[sl] = vec + (ok ? it_idx(kk, (long long)(di * g.N + jn) * Tp + tt) : 0);
       if (ok) h_ok |= 1u << sl;
       if (di < 0) h_up |= 1u << sl;
       if (di > 0) h_dn |= 1u << sl;
@@ -320,7 +327,8 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
     const bool ok = e < BN && tt <= g.T && (cjj == 0 || two_cols);
     const long long go = ((e / TT) % NS) * g.Ps + (long long)(j0 + cjj) * Tp + tt;
     if (vv == 0) {
-      bs_ptr[sl] = ok ? reinterpret_cast<const char*>(a.theta_out + go) : nullptr;
+      const long long gi = it_idx((e / TT) % NS, (long long)(j0 + cjj) * Tp + tt);
+      bs_ptr[sl] = ok ? reinterpret_cast<const char*>(a.theta_out + gi) : nullptr;
       bs_sm[sl] = w;
       bs_y |= 1u << sl;
     } else {
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       const unsigned hv = h_ok & (i == 0 ? ~h_up : ~0u) & (i + 1 >= g.K ? ~h_dn : ~0u);
 #pragma unroll
       for (int sl = 0; sl < HSL; ++sl)
-        if ((hv >> sl) & 1u) cp_async_elem(&sm.halo[b][0][0][0] + tid + sl * THR, h_ptr[sl] + rb);
+        if ((hv >> sl) & 1u) cp_async_elem(&sm.halo[b][0][0][0] + tid + sl * THR, h_ptr[sl] + rb * VS);
       const long long bb = (long long)i * g.N * RUN;
 #pragma unroll
       for (int sl = 0; sl < BSL; ++sl) {
@@ -394,7 +402,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
     for (int sl = 0; sl < BSLB; ++sl) {
       if (!((bs_ok >> sl) & 1u)) continue;
       if ((bs_y >> sl) & 1u)
-        cp_async_elem(&sm.ys[b][0][0][0] + bs_sm[sl], reinterpret_cast<const VT*>(bs_ptr[sl]) + rb);
+        cp_async_elem(&sm.ys[b][0][0][0] + bs_sm[sl], reinterpret_cast<const VT*>(bs_ptr[sl]) + rb * VS);
       else
         cp_async_8(&sm.src[b][0][0][0][0] + bs_sm[sl], reinterpret_cast<const double*>(bs_ptr[sl]) + rb);
     }
@@ -471,7 +479,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
             const VT* blk = pd.Om + (((size_t)p * 5 + o) * NS + k) * NS;
             const long long qb = (long long)qn * Tp + t;
 #pragma unroll
-            for (int c = 0; c < NS; ++c) tau += blk[c] * a.theta_in[c * g.Ps + qb];
+            for (int c = 0; c < NS; ++c) tau += blk[c] * a.theta_in[it_idx(c, qb)];
           }
         } else {
 #pragma unroll
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
         const VT tc = __shfl_sync(gmask, tau, jj * NS + c, GS);
         out += Qrow[c] * tc;
       }
-      if (node_ok) a.theta_out[kP + off] = out;
+      if (node_ok) a.theta_out[it_idx(k, off)] = out;
     } else {
       // y_i = tau_i - F2 y_{i-2} - F1 y_{i-1}, one chain of multiply-adds
       // (the FP64 pipe's issue rate, not its latency, bounds the sweep, so
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
 #pragma unroll
         for (int bb = 0; bb < G2; ++bb) yv -= row[bb] * ym1[bb];
       }
-      if (node_ok) a.theta_out[kP + off] = yv;
+      if (node_ok) a.theta_out[it_idx(k, off)] = yv;
       if (lane_ok) sm.xy[grp][al] = yv;
       __syncwarp(gmask);
 #pragma unroll
@@ -583,7 +591,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
         for (int bb = 0; bb < G2; ++bb) xv -= row[bb] * xp1[bb];
       }
       if (node_ok) {
-        a.theta_out[kP + off] = xv;
+        a.theta_out[it_idx(k, off)] = xv;
         if (MU) acc0 += (double)xv * r_own;
         if (flex_dot) acc1 += (double)xv * y_own;
       }
@@ -598,7 +606,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
 
   if (UPDATE) {
     double tot0, tot1;
-    if (grid_reduce2<true>(acc0, acc1, a.partials, &st->counters[kCntNorm], &tot0, &tot1)) {
+    if (grid_reduce2_at<true>(acc0, acc1, a.partials, &st->counters[kCntNorm], &tot0, &tot1, bid, nblocks)) {
       // the stop test of Algorithm 1, with the rule selected by stop_mode
       st->rnorm2 = tot0;
       st->rnorm_inf = tot1;
@@ -615,7 +623,7 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
   }
   if (MU) {
     double tot0, tot1;
-    if (grid_reduce2<false>(acc0, acc1, a.partials, &st->counters[kCntMu], &tot0, &tot1)) {
+    if (grid_reduce2_at<false>(acc0, acc1, a.partials, &st->counters[kCntMu], &tot0, &tot1, bid, nblocks)) {
       // Algorithm 1: mu^(i+1) and the ratio used for d^(i+1);
       // the mixed mode takes q^(i+1)'(r^(i+1) - r^(i)) / mu^(i), which equals
       // mu^(i+1) / mu^(i) for an exactly symmetric preconditioner
@@ -633,6 +641,12 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>())) nbjm_s
       }
     }
   }
+}
+
+template <int NS, int VAR, typename VT, int THR>
+__global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>()))
+    nbjm_sweep_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a, SolverState* st) {
+  nbjm_sweep_body<NS, VAR, VT, THR>(g, pd, a, st, blockIdx.x, gridDim.x);
 }
 
 template <int NS, typename VT, int THR>

@@ -20,7 +20,8 @@ OK, EINVAL, ENOTPD, ENOCONV, EBREAKDOWN, ECUDA, ENOMEM, ETIMEOUT = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ECUDA",
                 6: "ENOMEM", 7: "ETIMEOUT"}
 OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS, OPT_PRECONDITIONER, OPT_KAPPA = 1, 2, 3, 4, 5, 6
-OPT_SWEEP_THREADS = 7
+OPT_SWEEP_THREADS, OPT_SWEEP_STEPS = 7, 8
+BATCH_PERSISTENT, BATCH_THREADS, BATCH_USES_PERSISTENT = 1, 2, 3
 
 EXPORTED = (
     "lq2d_create", "lq2d_create_device", "lq2d_update", "lq2d_update_device", "lq2d_set_affine", "lq2d_solve",
@@ -28,6 +29,7 @@ EXPORTED = (
     "lq2d_apply_precond_multi_device", "lq2d_solve_multi_device",
     "lq2d_autotune",
     "lq2d_batch_create", "lq2d_batch_solve", "lq2d_batch_destroy", "lq2d_get_solution_device",
+    "lq2d_batch_set_option", "lq2d_batch_get_option", "lq2d_batch_autotune",
     "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
     "lq2d_wsnet_create", "lq2d_wsnet_param_count", "lq2d_wsnet_set_params", "lq2d_wsnet_get_params",
@@ -39,7 +41,7 @@ EXPORTED = (
 class Stats(ctypes.Structure):
     _fields_ = [
         ("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("status", ctypes.c_int),
-        ("sweep_launches", ctypes.c_int), ("delta_launches", ctypes.c_int), ("pad", ctypes.c_int),
+        ("sweep_launches", ctypes.c_int), ("delta_launches", ctypes.c_int), ("sweep_steps", ctypes.c_int),
         ("rel_residual", ctypes.c_double), ("rel_kkt_residual", ctypes.c_double),
         ("kkt_inf", ctypes.c_double), ("cost", ctypes.c_double),
         ("sweep_ms", ctypes.c_double), ("delta_ms", ctypes.c_double),
@@ -95,6 +97,9 @@ def load() -> ctypes.CDLL:
         "lq2d_batch_create": (i, [pp, i, _vp]),
         "lq2d_batch_solve": (i, [_vp, d, i, i, i, _vp, _vp, _vp, _vp]),
         "lq2d_batch_destroy": (None, [_vp]),
+        "lq2d_batch_set_option": (i, [_vp, i, i]),
+        "lq2d_batch_get_option": (i, [_vp, i, _ip]),
+        "lq2d_batch_autotune": (i, [_vp, i, i, i, _ip, _dp, _vp]),
         "lq2d_get_solution_device": (i, [_vp, _vp, _vp, _vp, _vp]),
         "lq2d_set_option": (i, [_vp, i, d]),
         "lq2d_get_stats": (i, [_vp, ctypes.POINTER(Stats)]),
@@ -325,6 +330,22 @@ class Batch:
         code = load().lq2d_batch_solve(self._h, tol, S, L, max_iter, its, rel, sts, _stream(stream))
         _check(code, allow)
         return dict(iterations=list(its), rel_kkt=list(rel), statuses=list(sts), status=code)
+
+    def set_option(self, option, value):
+        _check(load().lq2d_batch_set_option(self._h, option, int(value)))
+
+    def get_option(self, option):
+        v = ctypes.c_int(0)
+        _check(load().lq2d_batch_get_option(self._h, option, ctypes.byref(v)))
+        return v.value
+
+    def autotune(self, S=2, L=2, reps=3, stream=None):
+        """Chooses the persistent loop's sweep width by timing; returns
+        (threads, ms per D_S of the whole batch)."""
+        thr = ctypes.c_int(0)
+        ms = ctypes.c_double(0.0)
+        _check(load().lq2d_batch_autotune(self._h, S, L, reps, ctypes.byref(thr), ctypes.byref(ms), _stream(stream)))
+        return thr.value, ms.value
 
     def close(self):
         if self._h is not None and self._h.value:

@@ -144,3 +144,58 @@ def test_autotune_picks_a_width_and_keeps_results(dev):
         prob.set_option(lq2d.OPT_SWEEP_THREADS, 100)
     with pytest.raises(lq2d.LQ2DError):
         prob.autotune(2, 3, 1)
+
+
+def test_persistent_loop_equals_chains_single_solves_and_oracle(dev):
+    """The persistent batched loop (one launch per kernel of a PCG step for
+    every problem, work pulled from a device queue) gives each problem the
+    result of its own single solve with the same sweep width, bit for bit,
+    and the one-chain-per-problem graph gives the same; uneven K, N, T (odd N,
+    K = 1, N = 1 included)."""
+    lq2d = lq()
+    grids = synth.batch_grids(12, seed=23, K_range=(1, 11), N_range=(1, 12), T_range=(1, 30))
+    probs = [lq2d.Problem.from_grid(g) for g in grids]
+    batch = lq2d.Batch(probs)
+    for width in (32, 128, 64):
+        batch.set_option(lq2d.BATCH_THREADS, width)
+        out = batch.solve(1e-11, 2, 2, 5000)
+        assert batch.get_option(lq2d.BATCH_USES_PERSISTENT) == 1
+        assert out["status"] == 0
+        persistent = [costate_of(p, g, dev) for p, g in zip(probs, grids)]
+        for idx, (p, g) in enumerate(zip(probs, grids)):
+            p.set_option(lq2d.OPT_SWEEP_THREADS, width)
+            single = p.solve(1e-11, 2, 2, 5000)
+            assert single["iterations"] == out["iterations"][idx]
+            assert np.array_equal(single["costate"], persistent[idx])
+    batch.set_option(lq2d.BATCH_PERSISTENT, 0)
+    chains = batch.solve(1e-11, 2, 2, 5000)
+    assert batch.get_option(lq2d.BATCH_USES_PERSISTENT) == 0
+    assert chains["iterations"] == out["iterations"]
+    for p, g, lam in zip(probs, grids, persistent):
+        assert np.array_equal(costate_of(p, g, dev), lam)
+    for idx in (0, 5, len(grids) - 1):
+        g = grids[idx]
+        ref = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())).solve(1e-12)
+        assert np.linalg.norm(persistent[idx] - ref.delta) <= 1e-8 * np.linalg.norm(ref.delta)
+    batch.close()
+
+
+def test_batch_autotune_picks_a_width_and_the_batch_still_solves(dev):
+    lq2d = lq()
+    grids = synth.batch_grids(8, seed=29, K_range=(4, 16), N_range=(4, 16), T_range=(8, 40))
+    probs = [lq2d.Problem.from_grid(g) for g in grids]
+    batch = lq2d.Batch(probs)
+    threads, ms = batch.autotune(2, 2, 2)
+    assert threads in (32, 64, 128) and ms > 0
+    assert batch.get_option(lq2d.BATCH_THREADS) == threads
+    out = batch.solve(1e-10, 2, 2, 5000)
+    assert out["status"] == 0 and batch.get_option(lq2d.BATCH_USES_PERSISTENT) == 1
+    g = grids[3]
+    ref = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())).solve(1e-12)
+    assert np.linalg.norm(costate_of(probs[3], g, dev) - ref.delta) <= 1e-8 * np.linalg.norm(ref.delta)
+    with pytest.raises(lq2d.LQ2DError):
+        batch.set_option(lq2d.BATCH_THREADS, 256)
+    probs[0].set_precision(1)
+    with pytest.raises(lq2d.LQ2DError):
+        batch.autotune(2, 2, 1)
+    batch.close()

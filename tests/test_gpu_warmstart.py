@@ -213,3 +213,34 @@ def test_online_training_keeps_a_ring_buffer_of_solved_pairs(dev):
     with pytest.raises(ValueError):
         ws.fit_online(seeds, 1, group=8, buffer=12)
     ws.close()
+
+
+def test_network_of_the_full_architecture_reduces_iterations_on_128x128x100(dev):
+    """The learned warm start at its own size: 6 layers of 3 x 3 convolutions
+    with 64 channels on the K = N = 128, n = 4, m = 2, T = 100 family,
+    trained on 256 solver-generated pairs (grouped multi-right-hand-side
+    solves, a reduced training set), then held-out instances solved from the
+    network's guess and from zero in FP64: fewer PCG steps from the guess,
+    and the same costate within 1e-6 (Algorithm 1 accepts any delta^(0))."""
+    from paper_2304_04980_gb300 import warmstart
+    fam = synth.warmstart_family()
+    assert (fam.K, fam.N, fam.T, fam.n, fam.m) == (128, 128, 100, 4, 2)
+    ws = warmstart.WarmStart(fam, channels=64, layers=6, batch=8, seed=0)
+    ws.generate_grouped(range(1000, 1256), tol=1e-6, group=32)
+    sigma = float(ws.targets.std())
+    ws.net.close()
+    ws.net = lq().WarmStartNet(fam.K, fam.N, fam.T, fam.n, 64, 6, 8, sigma)
+    ws.net.set_params(synth.warmstart_init(ws.net.layer_sizes(), 0, 0.1))
+    losses = ws.fit(800, lr=1e-3, lr_final=5e-5)
+    assert losses[-50:].mean() < 0.2 * losses[:10].mean()
+    zero_its, warm_its = [], []
+    for seed in range(100000, 100008):
+        z = ws.solve(seed, tol=1e-8, warm=False)
+        w = ws.solve(seed, tol=1e-8, warm=True)
+        assert z["status"] == 0 and w["status"] == 0
+        diff = torch.linalg.norm(w["costate"] - z["costate"]) / torch.linalg.norm(z["costate"])
+        assert float(diff) <= 1e-6
+        zero_its.append(z["iterations"])
+        warm_its.append(w["iterations"])
+    assert np.mean(warm_its) < np.mean(zero_its)
+    ws.close()
