@@ -64,6 +64,11 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed mixed-precision comparison on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-threads", type=int, default=0, help="set LQ2D_OPT_SWEEP_THREADS (0: library default)")
+    ap.add_argument("--sweep-steps", type=int, default=-1,
+                    help="set LQ2D_OPT_SWEEP_STEPS, time steps per lane of the n = 4 FP32 sweeps (-1: default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default FP32 sweep schedule in the precision comparison")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle PCG steps in the all-cores CPU sample")
     ap.add_argument("--cpu-iters-one", type=int, default=1, help="oracle PCG steps in the one-thread CPU sample")
     ap.add_argument("--batch", type=int, default=0,
@@ -272,9 +277,17 @@ def measured_hbm_gbs():
         return 6800.0
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "fp64": ("sweep_tiled.cuh", "common.cuh", "kernels.h"),
+    "fp32": ("sweep_bulk.cuh", "sweep_bulk.cu", "sweep_tiled.cuh", "common.cuh", "kernels.h"),
+}
+
+
+def kernel_source_hash(precision="fp64"):
+    """Hash of the sources of the sweep kernels of one precision (the FP64
+    tiled sweep; the FP32 bulk-copy and tiled sweeps)."""
     h = hashlib.sha256()
-    for name in ("sweep_tiled.cuh", "common.cuh", "kernels.h"):
+    for name in KERNEL_SOURCES[precision]:
         h.update(open(os.path.join(ROOT, "paper_2304_04980_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -290,7 +303,7 @@ def profiled_traffic(workload, precision="fp64"):
     text = open(path).read()
     m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram bytes per launch \(read\+write\):\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(precision):
         return None
     return float(m_bytes.group(1))
 
@@ -456,6 +469,10 @@ def run_ours(args, dist):
             prob.set_precision(1 if args.precision == "mixed" else 2)
         if args.driver == "stream":
             prob.set_option(lq2d.OPT_DRIVER, 1)
+        if args.sweep_threads:
+            prob.set_option(lq2d.OPT_SWEEP_THREADS, args.sweep_threads)
+        if args.sweep_steps >= 0:
+            prob.set_option(lq2d.OPT_SWEEP_STEPS, args.sweep_steps)
         x = torch.empty((g.T + 1, g.nodes, g.n), dtype=torch.float64, device=dev)
         u = torch.empty((g.T, g.nodes, g.m), dtype=torch.float64, device=dev)
         lam = torch.empty_like(x)
@@ -556,12 +573,18 @@ def run_ours(args, dist):
             for mode, label in ((1, "mixed: FP32 preconditioner, FP64 residual/dots/updates"),
                                 (2, "mixed2: FP32 preconditioner and Delta product, FP64 residual replacement")):
                 prob.set_precision(mode)
+                # the library's autotuner picks the FP32 sweep schedule for this
+                # shape (outside the timed region, as a user would at set-up)
+                tuned = prob.autotune(2, 2, 3, stream=stream) if not args.no_autotune else None
                 for _ in range(args.warmup):
                     step()
                 c_ms, c_its, c_rels = timed(aux)
                 c_dev = sum(c_ms)
+                stt = prob.stats()
                 entry = {"precision": label, "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT,
                          "ms_per_step": c_dev / aux, "steps": aux,
+                         "sweep_schedule": {"threads": stt["sweep_threads"], "steps_per_lane": stt["sweep_steps"],
+                                            "autotuned": tuned is not None},
                          "iterations_per_solve": sum(c_its) / len(c_its), "rel_kkt_residual": max(c_rels),
                          "speedup_time_to_solve": (res["dev_ms"] / args.steps) / (c_dev / aux)}
                 prob.set_option(lq2d.OPT_TIMING, 1)

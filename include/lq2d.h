@@ -81,12 +81,14 @@ enum {
                                   Default 64; lq2d_autotune picks it by timing.  Results may
                                   differ in the last bits between widths (partial sums are
                                   grouped per CTA) */
-  LQ2D_OPT_SWEEP_STEPS = 8    /* 1, 2 or 4: time steps each lane carries in the n = 4 FP32 sweeps
-                                  (a CTA then holds threads/8 * steps time steps); the schedules
-                                  compiled are (threads, steps) = (32, 4), (64, 4), (64, 2),
-                                  (128, 2), (32, 2), (64, 1), and any other pair runs as (64, 4).
-                                  Default 4; lq2d_autotune picks the pair by timing.  No effect
-                                  on FP64 sweeps or other n */
+  LQ2D_OPT_SWEEP_STEPS = 8    /* 0, 1, 2 or 4: time steps each lane carries in the n = 4 FP32
+                                  sweeps with bulk-copy staging (a CTA then holds threads/8 * steps
+                                  time steps); 0 selects the tiled FP32 kernel (LQ2D_OPT_SWEEP_THREADS
+                                  as for FP64).  The bulk schedules compiled are (threads, steps) =
+                                  (32, 4), (64, 4), (64, 2), (128, 2), (32, 2), (64, 1); another pair
+                                  with steps >= 1 runs as (64, 4).  Default: 4 when the grid has at
+                                  least 16384 (column pair, time) blocks, else 0; lq2d_autotune picks
+                                  the pair by timing.  No effect on FP64 sweeps or other n */
 };
 
 /* Statistics of the last solve on a handle. */

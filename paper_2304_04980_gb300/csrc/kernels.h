@@ -139,7 +139,10 @@ void launch_sweep4_f32(int variant, int threads, int steps, const Grid& g, const
 bool sweep4_f32_config_ok(int threads, int steps);
 int sweep4_f32_configs(int (*out)[2], int cap);
 cudaError_t prepare_sweep4_f32();
-constexpr int kSweepSteps = 4;  // default time steps per lane of the n = 4 FP32 sweep
+constexpr int kSweepSteps = 4;  // time steps per lane of the n = 4 FP32 bulk-copy sweep by default
+// (column pair, time) blocks from which the n = 4 FP32 sweeps default to the
+// bulk-copy kernel (below: the tiled kernel, whose finer tiles fill the GPU)
+constexpr long long kBulkMinBlocks = 16384;
 
 // dimension-generic helpers (kernels_misc.cu)
 void launch_init_state(SolverState* st, double tol, int max_iter, int stop_mode, const double* bnorm2,

@@ -371,24 +371,27 @@ cudaError_t prepare_sweeps() {
                       prepare_sweeps_t<NS, double, 128>(), prepare_sweeps_t<NS, double, 256>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
-  if constexpr (NS == 4) {
-    // n = 4 runs its FP32 sweeps with bulk-copy staging (sweep_bulk.cu)
-    return prepare_sweep4_f32();
-  } else {
-    cudaError_t f[4] = {prepare_sweeps_t<NS, float, 32>(), prepare_sweeps_t<NS, float, 64>(),
-                        prepare_sweeps_t<NS, float, 128>(), prepare_sweeps_t<NS, float, 256>()};
-    for (cudaError_t x : f)
-      if (x != cudaSuccess) return x;
-    return cudaSuccess;
-  }
+  cudaError_t f[4] = {prepare_sweeps_t<NS, float, 32>(), prepare_sweeps_t<NS, float, 64>(),
+                      prepare_sweeps_t<NS, float, 128>(), prepare_sweeps_t<NS, float, 256>()};
+  for (cudaError_t x : f)
+    if (x != cudaSuccess) return x;
+  // n = 4 also has FP32 sweeps with bulk-copy staging (sweep_bulk.cu)
+  if constexpr (NS == 4) return prepare_sweep4_f32();
+  return cudaSuccess;
 }
 
-// FP32 sweep: the bulk-copy kernels for n = 4, the tiled kernel otherwise.
+// FP32 sweep: for n = 4 with steps >= 1 the bulk-copy kernels (a lane
+// carries `steps` time steps), else the tiled kernel.
 template <int NS>
 void launch_sweep_f32(int variant, int threads, int steps, const Grid& g, const PrecData<float>& pd,
                       const SweepArgsT<float>& a, SolverState* st, cudaStream_t s) {
-  if constexpr (NS == 4) launch_sweep4_f32(variant, threads, steps, g, pd, a, st, s);
-  else launch_sweep<NS, float>(variant, threads, g, pd, a, st, s);
+  if constexpr (NS == 4) {
+    if (steps >= 1) {
+      launch_sweep4_f32(variant, threads, steps, g, pd, a, st, s);
+      return;
+    }
+  }
+  launch_sweep<NS, float>(variant, threads, g, pd, a, st, s);
 }
 
 template <int NS>

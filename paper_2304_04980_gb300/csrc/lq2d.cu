@@ -216,6 +216,10 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   g.Pus = round_up(g.Pu, 64);
   h->kt = kernel_table(n);
   if (!h->kt) return fail(LQ2D_EINVAL, "no kernels for this n");
+  // n = 4 FP32 sweeps: the bulk-copy kernel (four time steps per lane) once
+  // the grid has enough (column pair, time) blocks to fill the GPU with its
+  // coarse tiles, else the tiled kernel
+  h->sweep_steps = (long long)g.V * (T + 1) >= kBulkMinBlocks ? kSweepSteps : 0;
   LQ_CUDA(h->kt->prepare());
   LQ_CUDA(cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking));
   const size_t NN = g.NN, nn = (size_t)n * n;
@@ -1683,10 +1687,10 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
   }
   // candidates: CTA widths, and for the n = 4 FP32 sweeps the compiled
   // (width, time steps per lane) schedules
-  int cand[8][2] = {{32, 1}, {64, 1}, {128, 1}, {256, 1}};
+  int cand[12][2] = {{32, 1}, {64, 1}, {128, 1}, {256, 1}};
   int ncand = 4;
   const bool bulk = slot == 1 && g.n == 4;
-  if (bulk) ncand = sweep4_f32_configs(cand, 8);
+  if (bulk) ncand = sweep4_f32_configs(cand, 12);
   const int saved_steps = h->sweep_steps;
   double best_ms = 0.0;
   int best = saved, best_steps = saved_steps;
@@ -1963,7 +1967,7 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
       h->sweep_threads[0] = h->sweep_threads[1] = v;
       return LQ2D_OK;
     case LQ2D_OPT_SWEEP_STEPS:
-      if (v != 1 && v != 2 && v != 4) return fail(LQ2D_EINVAL, "sweep steps must be 1, 2 or 4");
+      if (v != 0 && v != 1 && v != 2 && v != 4) return fail(LQ2D_EINVAL, "sweep steps must be 0, 1, 2 or 4");
       h->sweep_steps = v;
       return LQ2D_OK;
     default:

@@ -46,11 +46,14 @@ cudaError_t prepare_config() {
 
 }  // namespace
 
-// Schedules compiled for the n = 4 FP32 sweep: (threads per CTA, time steps
-// per lane).  A CTA holds threads/8 groups of 8 lanes, each group R
-// consecutive time steps of one column pair.
-constexpr int kBulkConfigs[][2] = {{32, 4}, {64, 4}, {64, 2}, {128, 2}, {32, 2}, {64, 1}};
-constexpr int kNumBulkConfigs = 6;
+// Schedules of the n = 4 FP32 sweep: (threads per CTA, time steps per
+// lane).  With steps >= 1 a CTA of the bulk-copy kernel holds threads/8
+// groups of 8 lanes, each group `steps` consecutive time steps of one column
+// pair; steps = 0 is the tiled kernel (one time step per group, per-element
+// cp.async staging), whose finer tiles suit small grids.
+constexpr int kBulkConfigs[][2] = {{32, 4}, {64, 4}, {64, 2}, {128, 2}, {32, 2}, {64, 1},
+                                   {32, 0}, {64, 0}, {128, 0}};
+constexpr int kNumBulkConfigs = 9;
 
 bool sweep4_f32_config_ok(int threads, int steps) {
   for (int c = 0; c < kNumBulkConfigs; ++c)
@@ -78,8 +81,8 @@ void launch_sweep4_f32(int variant, int threads, int steps, const Grid& g, const
 }
 
 cudaError_t prepare_sweep4_f32() {
-  const cudaError_t e[kNumBulkConfigs] = {prepare_config<4, 32>(), prepare_config<4, 64>(), prepare_config<2, 64>(),
-                                          prepare_config<2, 128>(), prepare_config<2, 32>(), prepare_config<1, 64>()};
+  const cudaError_t e[6] = {prepare_config<4, 32>(),  prepare_config<4, 64>(), prepare_config<2, 64>(),
+                            prepare_config<2, 128>(), prepare_config<2, 32>(), prepare_config<1, 64>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   return cudaSuccess;

@@ -23,7 +23,8 @@
 //    aligned supersets) is staged by one cp.async.bulk copy per contiguous
 //    run, completing on the step buffer's mbarrier, instead of one cp.async
 //    per element.
-//  * Three staging buffers keep two pair-rows in flight.  Every wait on an
+//  * Three staging buffers keep two pair-rows in flight (two buffers, one
+//    pair-row, when a lane carries four time steps).  Every wait on an
 //    mbarrier is bounded; a wait that runs out sets the solver state to the
 //    loop-cap status and a fault word, lets the copies in flight land
 //    (again bounded) and ends the CTA.
@@ -38,7 +39,12 @@ namespace hot {
 namespace bulk {
 
 constexpr int NS = 4, G2 = 8, BS = 64, REC = 6 * BS;  // record: [N2][N1][D^-1][F2][F1][L0^-1]
-constexpr int NB = 3;                                 // staging buffers
+// Staging buffers: three (two pair-rows in flight) when a lane carries one or
+// two time steps; two when it carries four, whose steps are long enough to
+// cover a copy's latency with one pair-row in flight, and whose shared
+// memory then allows six CTAs per SM.
+template <int R>
+constexpr int stages() { return R >= 4 ? 2 : 3; }
 // A wait gives up after kWaitCap rounds of try_wait, each suspending for at
 // most about kWaitHintNs: about a second in all.
 constexpr unsigned kWaitCap = 1u << 20;
@@ -136,18 +142,18 @@ struct Smem {
     float src32[2][G::HW][NS];            // forward: r_theta (FP32); backward: the forward result y_i
     double src64[G::NV][2][NS][G::RUN64]; // FP64 runs: r, y, d, delta (update); r (source); r, y (mu)
   };
-  Buf buf[NB];
+  Buf buf[stages<R>()];
   float xy[G::NG][R][G2];                 // per group: the step's result, exchanged inside the group
-  uint64_t bar[NB];
+  uint64_t bar[stages<R>()];
 };
 
-// Staging buffers per CTA: one CTA per SM fewer than shared memory allows.
+// CTAs per SM to budget registers for: as many as shared memory allows.
 template <int VAR, int R, int THR>
 constexpr int min_blocks() {
-  constexpr int by_smem = 232448 / ((int)sizeof(Smem<VAR, R, THR>) + 1024) - 1;
+  constexpr int by_smem = 232448 / ((int)sizeof(Smem<VAR, R, THR>) + 1024);
   constexpr int by_threads = 2048 / THR;
   constexpr int b = by_smem < by_threads ? by_smem : by_threads;
-  return b < 1 ? 1 : (b > 16 ? 16 : b);
+  return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
 
 constexpr int kMaxCopies = 48;  // bulk copies of one step, at most
@@ -164,6 +170,7 @@ __global__ void __launch_bounds__(THR, (bulk::min_blocks<VAR, R, THR>()))
   constexpr bool UPDATE = Gm::UPDATE, XI = Gm::XI, OMEGA = Gm::OMEGA, MU = Gm::MU;
   constexpr bool HALO = XI || OMEGA;
   constexpr bool XIOM = VAR == kSweepXiOmega;
+  constexpr int NB = stages<R>();
   constexpr int PD = NB - 1;
   constexpr int CPT = (kMaxCopies + THR - 1) / THR;
   extern __shared__ __align__(128) unsigned char bulk_smem[];

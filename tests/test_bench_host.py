@@ -40,19 +40,27 @@ def test_profiled_traffic_requires_the_current_kernel_hash(tmp_path, monkeypatch
     prof.mkdir()
     text = "kernel source hash: %s\ndram bytes per launch (read+write): 12345678\n"
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abcdef0123456789")
+    monkeypatch.setattr(bench, "kernel_source_hash",
+                        lambda precision="fp64": {"fp64": "abcdef0123456789", "fp32": "0123456789abcdef"}[precision])
     (prof / "nbjm_sweep_w.md").write_text(text % "abcdef0123456789")
     assert bench.profiled_traffic("w") == 12345678.0
     (prof / "nbjm_sweep_w.md").write_text(text % "0000000000000000")
     assert bench.profiled_traffic("w") is None
     assert bench.profiled_traffic("missing") is None
+    # the FP32 summary is keyed on the FP32 sweeps' own sources
+    (prof / "nbjm_sweep_f32_w.md").write_text(text % "0123456789abcdef")
+    assert bench.profiled_traffic("w", "fp32") == 12345678.0
+    (prof / "nbjm_sweep_f32_w.md").write_text(text % "abcdef0123456789")
+    assert bench.profiled_traffic("w", "fp32") is None
 
 
 def test_kernel_hash_covers_the_sweep_sources():
-    h = bench.kernel_source_hash()
-    assert len(h) == 16 and int(h, 16) >= 0
-    for name in ("sweep_tiled.cuh", "common.cuh", "kernels.h"):
-        assert os.path.exists(os.path.join(bench.ROOT, "paper_2304_04980_gb300", "csrc", name))
+    for precision in ("fp64", "fp32"):
+        h = bench.kernel_source_hash(precision)
+        assert len(h) == 16 and int(h, 16) >= 0
+        for name in bench.KERNEL_SOURCES[precision]:
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_2304_04980_gb300", "csrc", name))
+    assert bench.kernel_source_hash("fp64") != bench.kernel_source_hash("fp32")
 
 
 def test_clock_stop_ends_the_sampler_and_parses_its_file(tmp_path):

@@ -199,3 +199,51 @@ def test_batch_autotune_picks_a_width_and_the_batch_still_solves(dev):
     with pytest.raises(lq2d.LQ2DError):
         batch.autotune(2, 2, 1)
     batch.close()
+
+
+FP32_SCHEDULES = [(32, 4), (64, 4), (64, 2), (128, 2), (32, 2), (64, 1), (32, 0), (64, 0), (128, 0)]
+BULK_SHAPES = [(5, 7, 33, 4, 2), (1, 3, 9, 4, 2), (4, 4, 1, 4, 2), (3, 2, 2, 4, 2), (6, 5, 70, 4, 1),
+               (2, 9, 4, 4, 2)]
+
+
+@pytest.mark.parametrize("shape", BULK_SHAPES, ids=["K%dN%dT%d" % s[:3] for s in BULK_SHAPES])
+def test_fp32_schedules_match_oracle(dev, shape):
+    """Every compiled schedule of the n = 4 FP32 sweeps (bulk-copy kernel with
+    1, 2 or 4 time steps per lane at several CTA widths, and the tiled kernel)
+    gives the oracle's D_S r (Algorithm 2, S x L sweeps) within the FP32 bound,
+    for (S, L) in {(1, 2), (2, 2), (3, 4)}, on odd N, K = 1, T = 1 and 2 and
+    ragged tiles; a mixed-precision solve with each schedule reaches the
+    oracle's solution."""
+    lq2d = lq()
+    K, N, T, n, m = shape
+    g = synth.random_grid(K, N, T, n, m, seed=900 + 7 * K + 3 * N + T)
+    orc = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays()))
+    lam = orc.solve(1e-12).delta
+    prob = lq2d.Problem.from_grid(g)
+    prob.set_precision(1)
+    r = synth.random_vector((g.T + 1, g.nodes, g.n), seed=6)
+    rt = torch.from_numpy(r).to(dev)
+    refs = {SL: orc.preconditioner(*SL).apply(r.ravel()) for SL in ((1, 2), (2, 2), (3, 4))}
+    for thr, steps in FP32_SCHEDULES:
+        prob.set_option(lq2d.OPT_SWEEP_THREADS, thr)
+        prob.set_option(lq2d.OPT_SWEEP_STEPS, steps)
+        st = prob.stats()
+        assert (st["sweep_threads"], st["sweep_steps"]) == (thr, steps)
+        for SL, ref in refs.items():
+            q = torch.empty_like(rt)
+            prob.apply_precond_device(SL[0], SL[1], rt, q)
+            got = q.cpu().numpy().ravel()
+            assert np.isfinite(got).all()
+            assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), (thr, steps, SL)
+        for mode in (1, 2):
+            prob.set_precision(mode)
+            out = prob.solve(1e-10, 2, 2, 5000)
+            assert out["status"] == 0, (thr, steps, mode)
+            assert np.linalg.norm(out["costate"] - lam) <= 1e-7 * np.linalg.norm(lam), (thr, steps, mode)
+        prob.set_precision(1)
+    with pytest.raises(lq2d.LQ2DError):
+        prob.set_option(lq2d.OPT_SWEEP_STEPS, 3)
+    thr, ms = prob.autotune(2, 2, 2)
+    st = prob.stats()
+    assert (st["sweep_threads"], st["sweep_steps"]) in FP32_SCHEDULES and thr == st["sweep_threads"]
+    prob.close()
