@@ -215,6 +215,16 @@ def band_solve_flops(K, n, cols):
     return 2 * f
 
 
+def sweep_kernel_name(sched, vt):
+    """The sweep kernel a schedule runs: the bulk-copy FP32 kernel (n = 4,
+    steps per lane >= 1), the two-ended tiled kernel, or the tiled kernel."""
+    if vt == "float" and sched.get("steps_per_lane", 0) >= 1:
+        return "nbjm_sweep_bulk_kernel<*,%d,%d>" % (sched["steps_per_lane"], sched["threads"])
+    if sched.get("two_ended"):
+        return "nbjm_sweep_twisted_kernel<4,*,%s,%d>" % (vt, sched["threads"])
+    return "nbjm_sweep_kernel<4,*,%s,%d>" % (vt, sched["threads"])
+
+
 def sweep_flops(g: synth.GridLQ):
     """Algorithmic flops of one sweep launch of each kind, keyed by variant."""
     K, N, T, n = g.K, g.N, g.T, g.n
@@ -292,10 +302,11 @@ def kernel_source_hash(precision="fp64"):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, precision="fp64"):
+def profiled_traffic(workload, precision="fp64", kernel=None):
     """DRAM bytes per sweep launch from the committed ncu summary of that
     workload and sweep precision, if it was taken on the current kernel
-    source (else None)."""
+    source and, where the summary names its kernel, on `kernel` (else
+    None)."""
     name = "nbjm_sweep_%s.md" % workload if precision == "fp64" else "nbjm_sweep_f32_%s.md" % workload
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
@@ -304,6 +315,9 @@ def profiled_traffic(workload, precision="fp64"):
     m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram bytes per launch \(read\+write\):\s*([0-9.eE+]+)", text)
     if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(precision):
+        return None
+    m_kernel = re.search(r"profiled kernel:\s*(\S+)", text)
+    if kernel is not None and m_kernel and m_kernel.group(1) != kernel:
         return None
     return float(m_bytes.group(1))
 
@@ -496,6 +510,11 @@ def run_ours(args, dist):
             torch.cuda.synchronize()
             return [a.elapsed_time(b) for a, b in evs], its, rls
 
+        # the library's autotuner picks the sweep schedule of this precision
+        # for the shape (outside the timed region, as a user would at set-up)
+        tuned = None
+        if not args.no_autotune and not (args.sweep_threads or args.sweep_steps >= 0):
+            tuned = prob.autotune(2, 2, 3, stream=stream)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -515,6 +534,9 @@ def run_ours(args, dist):
         torch.cuda.synchronize()
         w1 = time.perf_counter()
         res["clocks"] = clocks.stop() if clocks else None
+        stt = prob.stats()
+        res["schedule"] = {"threads": stt["sweep_threads"], "steps_per_lane": stt["sweep_steps"],
+                           "two_ended": int(prob.get_option(lq2d.OPT_TWISTED)), "autotuned": tuned is not None}
         res["launches"] = prob.stats()["launches_total"] - launches0
         res["dev_ms"] = sum(step_ms)
         res["iters"] = iters
@@ -542,9 +564,9 @@ def run_ours(args, dist):
         if args.precision == "fp64":
             achieved = fl_total / (sweep_ms / 1e3) / 1e12
             res["roofline"] = {
-                "kernel": "nbjm_sweep_kernel<4,*,double>", "bound": "alu", "achieved": achieved,
+                "kernel": sweep_kernel_name(res["schedule"], "double"), "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": profiled_traffic(workload, "fp64"),
+                "traffic": profiled_traffic(workload, "fp64", sweep_kernel_name(res["schedule"], "double")),
                 "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
                 "flops_per_launch": fl_total / max(sweep_launches, 1),
                 "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
@@ -555,8 +577,10 @@ def run_ours(args, dist):
             peak = measured_hbm_gbs()
             achieved = by_total / (sweep_ms / 1e3) / 1e9
             res["roofline"] = {
-                "kernel": "nbjm_sweep_kernel<4,*,float>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(workload, "fp32"),
+                "kernel": sweep_kernel_name(res["schedule"], "float"), "bound": "hbm", "achieved": achieved,
+                "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(workload, "fp32", sweep_kernel_name(res["schedule"], "float")),
                 "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches_timed": sweep_launches,
                 "bytes_per_launch": by_total / max(sweep_launches, 1),
                 "fp32_tflops": fl_total / (sweep_ms / 1e3) / 1e12,
@@ -575,7 +599,8 @@ def run_ours(args, dist):
                 prob.set_precision(mode)
                 # the library's autotuner picks the FP32 sweep schedule for this
                 # shape (outside the timed region, as a user would at set-up)
-                tuned = prob.autotune(2, 2, 3, stream=stream) if not args.no_autotune else None
+                tuned = (prob.autotune(2, 2, 3, stream=stream)
+                         if not args.no_autotune and not (args.sweep_threads or args.sweep_steps >= 0) else None)
                 for _ in range(args.warmup):
                     step()
                 c_ms, c_its, c_rels = timed(aux)
@@ -584,6 +609,7 @@ def run_ours(args, dist):
                 entry = {"precision": label, "value": sum(c_its) / (c_dev / 1e3), "unit": UNIT,
                          "ms_per_step": c_dev / aux, "steps": aux,
                          "sweep_schedule": {"threads": stt["sweep_threads"], "steps_per_lane": stt["sweep_steps"],
+                                            "two_ended": int(prob.get_option(lq2d.OPT_TWISTED)),
                                             "autotuned": tuned is not None},
                          "iterations_per_solve": sum(c_its) / len(c_its), "rel_kkt_residual": max(c_rels),
                          "speedup_time_to_solve": (res["dev_ms"] / args.steps) / (c_dev / aux)}
@@ -599,9 +625,11 @@ def run_ours(args, dist):
                 prob.set_option(lq2d.OPT_TIMING, 0)
                 peak = measured_hbm_gbs()
                 ach = b_tot / (s_ms / 1e3) / 1e9
-                entry["sweep_roofline"] = {"kernel": "nbjm_sweep_kernel<4,*,float>", "bound": "hbm",
+                entry["sweep_roofline"] = {"kernel": sweep_kernel_name(entry["sweep_schedule"], "float"),
+                                           "bound": "hbm",
                                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                                           "traffic": profiled_traffic(workload, "fp32"),
+                                           "traffic": profiled_traffic(workload, "fp32", sweep_kernel_name(
+                                               entry["sweep_schedule"], "float")),
                                            "avg_launch_ms": s_ms / max(s_n, 1),
                                            "bytes_per_launch": b_tot / max(s_n, 1)}
                 compare.append(entry)
@@ -648,7 +676,7 @@ def run_ours(args, dist):
                   "value": sum(o["iters"]) / (o["dev_ms"] / 1e3), "unit": UNIT, "steps": args.steps,
                   "time_to_solve_ms": o["dev_ms"] / args.steps,
                   "iterations_per_solve": sum(o["iters"]) / len(o["iters"]), "rel_kkt_residual": max(o["rels"]),
-                  "roofline": o["roofline"], "compare_precision": o["compare"]}
+                  "roofline": o["roofline"], "sweep_schedule": o["schedule"], "compare_precision": o["compare"]}
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -670,6 +698,7 @@ def run_ours(args, dist):
             "rel_kkt_residual": max(main["rels"]),
             "wall_ms": main["wall_ms"],
             "roofline": main["roofline"],
+            "sweep_schedule": main["schedule"],
             "compare_precision": main["compare"],
             "also": second,
             "cpu_baseline": cpu,

@@ -81,7 +81,7 @@ enum {
                                   Default 64; lq2d_autotune picks it by timing.  Results may
                                   differ in the last bits between widths (partial sums are
                                   grouped per CTA) */
-  LQ2D_OPT_SWEEP_STEPS = 8    /* 0, 1, 2 or 4: time steps each lane carries in the n = 4 FP32
+  LQ2D_OPT_SWEEP_STEPS = 8,   /* 0, 1, 2 or 4: time steps each lane carries in the n = 4 FP32
                                   sweeps with bulk-copy staging (a CTA then holds threads/8 * steps
                                   time steps); 0 selects the tiled FP32 kernel (LQ2D_OPT_SWEEP_THREADS
                                   as for FP64).  The bulk schedules compiled are (threads, steps) =
@@ -89,6 +89,15 @@ enum {
                                   with steps >= 1 runs as (64, 4).  Default: 4 when the grid has at
                                   least 16384 (column pair, time) blocks, else 0; lq2d_autotune picks
                                   the pair by timing.  No effect on FP64 sweeps or other n */
+  LQ2D_OPT_TWISTED = 9        /* 1 (default where it applies): solve each Phi_bar block from both
+                                  ends at once (Section IV-B's banded solve with the pair-rows
+                                  eliminated from the first and the last towards two interface
+                                  rows, whose 2x2-block Schur complement is inverted at setup):
+                                  half the dependent chain of a sweep and twice its warps.  It
+                                  applies to the tiled sweeps of n = 4 with K >= 4 at widths 32
+                                  and 64; other schedules, and other n or K, stay one-sided.  The
+                                  handle keeps the reversed factor for it (one more factor's
+                                  memory).  0: one-sided.  lq2d_autotune tries both */
 };
 
 /* Statistics of the last solve on a handle. */
@@ -321,10 +330,12 @@ void lq2d_batch_destroy(lq2d_batch *b);
  * Delta product (two kernels) and one launch per NBJM sweep for all
  * problems, each a single wave of CTAs sized by occupancy that pull
  * (problem, node-time block) or (problem, column pair, time tile) units from
- * a device work queue; problems that have stopped skip their units.  Each
- * problem's arithmetic and reductions are those of its single solve with the
- * same sweep width, so the results are equal bit for bit.  Other batches
- * keep one chain per problem in the graph. */
+ * a device work queue; problems that have stopped skip their units.  Its
+ * sweeps are one-sided (the queue fills the GPU without the two-ended
+ * solve's extra warps): each problem's arithmetic and reductions are those
+ * of its single solve with the same sweep width and LQ2D_OPT_TWISTED = 0,
+ * so those results are equal bit for bit.  Other batches keep one chain per
+ * problem in the graph, with each problem's own options. */
 enum {
   LQ2D_BATCH_PERSISTENT = 1,      /* 1 (default): use the persistent loop when the problems allow it; 0: never */
   LQ2D_BATCH_THREADS = 2,         /* CTA width of its sweeps: 32, 64 (default) or 128 */
@@ -350,6 +361,10 @@ int lq2d_batch_autotune(lq2d_batch *b, int outer_S, int inner_L, int reps, int *
 int lq2d_get_solution_device(lq2d_problem *h, void *d_x, void *d_u, void *d_costate, void *stream);
 
 int lq2d_set_option(lq2d_problem *h, int option, double value);
+/* The current value of an option (LQ2D_OPT_SWEEP_THREADS and
+ * LQ2D_OPT_TWISTED: as the current precision mode's sweeps use it, e.g.
+ * after lq2d_autotune).  LQ2D_EINVAL for an unknown option or NULL. */
+int lq2d_get_option(const lq2d_problem *h, int option, double *value);
 int lq2d_get_stats(const lq2d_problem *h, lq2d_stats *out);
 
 /* Precision of the preconditioner (Algorithm 2) and of the Delta product.

@@ -42,6 +42,11 @@ struct PrecData {
   // FP32, n = 4: records of Phi_bar_{v,0} = blkdiag(Q^-1) in the layout of
   // fac ([V][K] records, F = N = 0, D^-1 = blkdiag(Q, Q)); NULL otherwise
   const VT* fac_t0;
+  // two-ended solve (when enabled): the factor of the reversed pair-row
+  // order (layout of fac, records in step order) and S^-1 of the interface
+  // rows per (v, class), [V][2][(4n)^2]; NULL otherwise
+  const VT* fac_rev;
+  const VT* sinv;
 };
 
 // Layout of the preconditioner's FP32 iterates (theta, delta^(s) and its

@@ -333,11 +333,51 @@ void launch_sweep_t(int variant, const Grid& g, const PrecData<VT>& pd, const Sw
   }
 }
 
+// The two-ended (twisted) sweep: CTAs of 2 THR threads, same tiles.
+template <int NS, typename VT, int THR>
+void launch_sweep_twisted_t(int variant, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a,
+                            SolverState* st, cudaStream_t s) {
+  const unsigned blocks = sweep_blocks<NS, THR>(g);
+  const size_t shm = sweep_twisted_smem_bytes<NS, VT, THR>();
+  switch (variant) {
+    case kSweepPlain: nbjm_sweep_twisted_kernel<NS, kSweepPlain, VT, THR><<<blocks, 2 * THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepUpdate: nbjm_sweep_twisted_kernel<NS, kSweepUpdate, VT, THR><<<blocks, 2 * THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepOmega: nbjm_sweep_twisted_kernel<NS, kSweepOmega, VT, THR><<<blocks, 2 * THR, shm, s>>>(g, pd, a, st); break;
+    case kSweepOmegaMu: nbjm_sweep_twisted_kernel<NS, kSweepOmegaMu, VT, THR><<<blocks, 2 * THR, shm, s>>>(g, pd, a, st); break;
+    default: nbjm_sweep_twisted_kernel<NS, kSweepXi, VT, THR><<<blocks, 2 * THR, shm, s>>>(g, pd, a, st); break;
+  }
+}
+
+template <int NS, typename VT, int THR>
+cudaError_t prepare_twisted_t() {
+  const int shm = (int)sweep_twisted_smem_bytes<NS, VT, THR>();
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, shm);
+    if (r != cudaSuccess) e = r;
+  };
+  set((const void*)nbjm_sweep_twisted_kernel<NS, kSweepPlain, VT, THR>);
+  set((const void*)nbjm_sweep_twisted_kernel<NS, kSweepUpdate, VT, THR>);
+  set((const void*)nbjm_sweep_twisted_kernel<NS, kSweepOmega, VT, THR>);
+  set((const void*)nbjm_sweep_twisted_kernel<NS, kSweepOmegaMu, VT, THR>);
+  set((const void*)nbjm_sweep_twisted_kernel<NS, kSweepXi, VT, THR>);
+  return e;
+}
+
 // Sweep launch with the CTA width (threads) chosen for the problem: 32, 64,
-// 128 or 256 threads, i.e. a tile of threads/GS time steps per CTA.
+// 128 or 256 threads, i.e. a tile of threads/GS time steps per CTA.  The
+// two-ended solve (pd.sinv set, n = 4, widths 32 and 64, every variant but
+// the standalone solver's first sweep) runs CTAs of twice that width.
 template <int NS, typename VT>
 void launch_sweep(int variant, int threads, const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a,
                   SolverState* st, cudaStream_t s) {
+  if constexpr (NS == 4) {
+    if (pd.sinv != nullptr && variant != kSweepXiOmega && (threads == 32 || threads == 64)) {
+      if (threads == 32) launch_sweep_twisted_t<NS, VT, 32>(variant, g, pd, a, st, s);
+      else launch_sweep_twisted_t<NS, VT, 64>(variant, g, pd, a, st, s);
+      return;
+    }
+  }
   switch (threads) {
     case 32: launch_sweep_t<NS, VT, 32>(variant, g, pd, a, st, s); break;
     case 64: launch_sweep_t<NS, VT, 64>(variant, g, pd, a, st, s); break;
@@ -375,8 +415,14 @@ cudaError_t prepare_sweeps() {
                       prepare_sweeps_t<NS, float, 128>(), prepare_sweeps_t<NS, float, 256>()};
   for (cudaError_t x : f)
     if (x != cudaSuccess) return x;
-  // n = 4 also has FP32 sweeps with bulk-copy staging (sweep_bulk.cu)
-  if constexpr (NS == 4) return prepare_sweep4_f32();
+  if constexpr (NS == 4) {
+    // n = 4 also has two-ended sweeps and FP32 sweeps with bulk-copy staging
+    cudaError_t t[4] = {prepare_twisted_t<NS, double, 32>(), prepare_twisted_t<NS, double, 64>(),
+                        prepare_twisted_t<NS, float, 32>(), prepare_twisted_t<NS, float, 64>()};
+    for (cudaError_t x : t)
+      if (x != cudaSuccess) return x;
+    return prepare_sweep4_f32();
+  }
   return cudaSuccess;
 }
 

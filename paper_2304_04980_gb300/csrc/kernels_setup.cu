@@ -273,8 +273,20 @@ __global__ void setup_omega_kernel(SetupBuffers sb, int K, int N, int n) {
 //   [F2_i][F1_i][L0_i^-1]  (forward step i; the sweeps read F2 and F1, the
 //                           multi-right-hand-side path applies D_i^-1 as
 //                           L0_i^-T L0_i^-1 in TF32)
+//
+// rev = 1 runs the same recurrences over the pair-rows in reverse order
+// (step i factors physical pair-row K-1-i, whose "previous" rows are the ones
+// below it), storing its records in step order in `out`: the factor of the
+// two-ended (twisted) solve's bottom half.  With iface != NULL the pass keeps
+// the blocks the interface rows k, k+1 (k = kI) need for their Schur
+// complement, [V][2][9] blocks of (2n)^2 (slot: 0 C_k, 1 tmp_{k+1},
+// 2 R_{k+1}, 3 A_kk, 4 A_{k+1,k+1}, 5 A_{k+1,k} from the forward pass;
+// 6 C, 7 tmp, 8 R of the reversed pass at physical rows k+1, k, k), where
+// C is the pivot block before its Cholesky, tmp = A_{i,prev} - L2 L1_prev'
+// and R = A_ii - L2 L2'.
 __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V, long long fac_rec,
-                                    long long fac_vc, int* status) {
+                                    long long fac_vc, int* status, int rev, double* out, double* iface,
+                                    int kI) {
   extern __shared__ double smem[];
   const int vc = blockIdx.x;
   const int v = vc >> 1, cls = vc & 1;
@@ -297,18 +309,20 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
   int cur = 0;  // index of the L0^-1 of pair-row i-1 inside prevL0
   __syncwarp();
   for (int i = 0; i < K; ++i) {
-    // --- assemble the three blocks of row i of Phi_bar
+    const int ip = rev ? K - 1 - i : i;  // physical pair-row of step i
+    // --- assemble the three blocks of row ip of Phi_bar (towards the rows
+    //     of steps i-1 and i-2)
     for (int e = lane; e < 3 * BS; e += 32) {
       const int blk = e / BS, rc = e % BS;
       const int a = rc / G2, b = rc % G2;
       const int ja = a / n, ka = a % n, jb = b / n, kb = b % n;
-      const int di = -blk;  // column node lives in pair-row i - blk
+      const int di = rev ? blk : -blk;  // column node lives in pair-row ip + di
       double val = 0.0;
       const bool colA = (ja == 0) || two_cols;
       const bool colB = (jb == 0) || two_cols;
-      if (i + di >= 0) {
+      if (ip + di >= 0 && ip + di < K) {
         if (colA && colB) {
-          const int p = i * N + 2 * v + ja;
+          const int p = ip * N + 2 * v + ja;
           const int o = off13_index(di, jb - ja);
           if (o >= 0) val = sb.M13[((size_t)p * 13 + o) * nn + ka * n + kb];
           if (blk == 0 && ja == jb) val += Qd[(size_t)p * nn + ka * n + kb] + sb.Sb[(size_t)p * nn + ka * n + kb];
@@ -356,6 +370,32 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       C[e] = s;
     }
     __syncwarp();
+    // --- interface blocks of the two-ended solve (see above)
+    if (iface != nullptr) {
+      double* ib = iface + (size_t)vc * 9 * BS;
+      const int at_k = rev ? K - kI - 1 : kI;      // step of physical row k
+      const int at_k1 = rev ? K - kI - 2 : kI + 1; // step of physical row k+1
+      const bool cap_c = rev ? (i == at_k1) : (i == at_k);
+      const bool cap_t = rev ? (i == at_k) : (i == at_k1);
+      for (int e = lane; e < BS; e += 32) {
+        if (cap_c) {
+          ib[(rev ? 6 : 0) * BS + e] = C[e];
+          if (!rev) ib[3 * BS + e] = Aii[e];
+        }
+        if (cap_t) {
+          const int a = e / G2, b = e % G2;
+          double r2 = Aii[e];
+          for (int c = 0; c < G2; ++c) r2 -= L2[a * G2 + c] * L2[b * G2 + c];
+          ib[(rev ? 7 : 1) * BS + e] = tmp[e];
+          ib[(rev ? 8 : 2) * BS + e] = r2;
+          if (!rev) {
+            ib[4 * BS + e] = Aii[e];
+            ib[5 * BS + e] = Aim1[e];
+          }
+        }
+      }
+      __syncwarp();
+    }
     // --- C = L0 L0' (right-looking, in place, lower triangle)
     for (int jc = 0; jc < G2; ++jc) {
       if (lane == 0) {
@@ -390,7 +430,7 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
     __syncwarp();
     // --- backward blocks of the two previous records, now that F1_i and
     //     F2_i exist: N1_{i-1} = F1_i', N2_{i-2} = F2_i'
-    double* rec_base = sb.fac + (size_t)vc * fac_vc;
+    double* rec_base = out + (size_t)vc * fac_vc;
     if (i >= 1) {
       double* rp = rec_base + (size_t)(i - 1) * fac_rec;
       for (int e = lane; e < BS; e += 32) rp[1 * BS + e] = F1[(e % G2) * G2 + e / G2];
@@ -436,6 +476,63 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
   (void)V;
 }
 
+// Interface of the two-ended solve of Phi_bar_{v,class}: rows k, k+1 after
+// eliminating rows 0..k-1 from the top and K-1..k+2 from the bottom,
+//   S = A_II - A_IT A_TT^-1 A_TI - A_IB A_BB^-1 A_BI   (4n x 4n, SPD),
+// from the blocks the two factor passes kept:
+//   S_kk = C_k + R'_k - A_kk,  S_{k+1,k+1} = R_{k+1} + C'_{k+1} - A_{k+1,k+1},
+//   S_{k+1,k} = tmp_{k+1} + tmp'_k' - A_{k+1,k}
+// (unprimed: forward pass, primed: reversed pass); stored inverted,
+// [V][2][(4n)^2].  One warp per (v, class), Gauss-Jordan without pivoting.
+__global__ void setup_interface_kernel(const double* iface, double* sinv, int n, int* status) {
+  extern __shared__ double smem[];
+  const int vc = blockIdx.x, lane = threadIdx.x;
+  const int G2 = 2 * n, BS = G2 * G2, W = 2 * G2, W2 = 2 * W;
+  const double* ib = iface + (size_t)vc * 9 * BS;
+  double* a = smem;  // [W][2W]: S | I
+  for (int e = lane; e < W * W2; e += 32) {
+    const int r = e / W2, c = e % W2;
+    double val;
+    if (c >= W) {
+      val = (c - W == r) ? 1.0 : 0.0;
+    } else {
+      const int hr = r / G2, hc = c / G2, rr = r % G2, cc = c % G2;
+      if (hr == 0 && hc == 0) val = ib[0 * BS + rr * G2 + cc] + ib[8 * BS + rr * G2 + cc] - ib[3 * BS + rr * G2 + cc];
+      else if (hr == 1 && hc == 1)
+        val = ib[2 * BS + rr * G2 + cc] + ib[6 * BS + rr * G2 + cc] - ib[4 * BS + rr * G2 + cc];
+      else if (hr == 1)  // (k+1, k)
+        val = ib[1 * BS + rr * G2 + cc] + ib[7 * BS + cc * G2 + rr] - ib[5 * BS + rr * G2 + cc];
+      else  // (k, k+1): the transpose of (k+1, k)
+        val = ib[1 * BS + cc * G2 + rr] + ib[7 * BS + rr * G2 + cc] - ib[5 * BS + cc * G2 + rr];
+    }
+    a[e] = val;
+  }
+  __syncwarp();
+  __shared__ int bad;
+  if (lane == 0) bad = 0;
+  __syncwarp();
+  for (int p = 0; p < W; ++p) {
+    const double piv = a[p * W2 + p];
+    if (lane == 0 && (!(piv > 0.0) || !isfinite(piv))) bad = 1;
+    const double ip = 1.0 / (piv > 0.0 ? piv : 1.0);
+    __syncwarp();
+    for (int c = lane; c < W2; c += 32) a[p * W2 + c] *= ip;
+    __syncwarp();
+    for (int e = lane; e < W * W2; e += 32) {
+      const int r = e / W2, c = e % W2;
+      if (r == p || c == p) continue;
+      a[e] -= a[r * W2 + p] * a[p * W2 + c];
+    }
+    __syncwarp();
+    for (int r = lane; r < W; r += 32)
+      if (r != p) a[r * W2 + p] = 0.0;
+    __syncwarp();
+  }
+  double* out = sinv + (size_t)vc * W * W;
+  for (int e = lane; e < W * W; e += 32) out[e] = a[(e / W) * W2 + W + e % W];
+  if (lane == 0 && bad) atomicOr(status, kSetupPhiNotPD);
+}
+
 void launch_setup(const SetupBuffers& sb, int K, int N, int n, int m, int V, long long fac_rec,
                   long long fac_vc, int* d_status, cudaStream_t s) {
   const int NN = K * N;
@@ -444,7 +541,16 @@ void launch_setup(const SetupBuffers& sb, int K, int N, int n, int m, int V, lon
   setup_m13_kernel<<<(NN * 13 + 127) / 128, 128, 0, s>>>(sb, K, N, n);
   setup_omega_kernel<<<(NN * 5 + 127) / 128, 128, 0, s>>>(sb, K, N, n);
   const size_t shm = (size_t)11 * (2 * n) * (2 * n) * sizeof(double);
-  setup_factor_kernel<<<V * 2, 32, shm, s>>>(sb, K, N, n, V, fac_rec, fac_vc, d_status);
+  const bool twisted = sb.fac_rev != nullptr && sb.iface != nullptr && sb.sinv != nullptr && K >= kTwistedMinK;
+  const int kI = (K - 2) / 2;
+  setup_factor_kernel<<<V * 2, 32, shm, s>>>(sb, K, N, n, V, fac_rec, fac_vc, d_status, 0, sb.fac,
+                                             twisted ? sb.iface : nullptr, kI);
+  if (twisted) {
+    setup_factor_kernel<<<V * 2, 32, shm, s>>>(sb, K, N, n, V, fac_rec, fac_vc, d_status, 1, sb.fac_rev,
+                                               sb.iface, kI);
+    const size_t shi = (size_t)(4 * n) * (8 * n) * sizeof(double);
+    setup_interface_kernel<<<V * 2, 32, shi, s>>>(sb.iface, sb.sinv, n, d_status);
+  }
 }
 
 }  // namespace lq2d

@@ -1,6 +1,7 @@
 // C-ABI library: problem handle, setup, and the PCG driver (Algorithm 1 with
 // Algorithm 2 as preconditioner) over the CUDA kernels of this directory.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -34,7 +35,7 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 struct GraphEntry {
-  int S = 0, L = 0, precision = 0, precond = 0, threads = 0;
+  int S = 0, L = 0, precision = 0, precond = 0, threads = 0, steps = 0, twisted = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -95,6 +96,10 @@ struct lq2d_problem {
   int precond_kind = 0;      // 0: NBJM (Algorithm 2), 1: none (plain CG)
   int sweep_threads[2] = {kSweepThreads, kSweepThreads};  // CTA width of the FP64 / FP32 sweeps (32..256)
   int sweep_steps = kSweepSteps;  // time steps per lane of the n = 4 FP32 sweeps
+  int twisted[2] = {0, 0};        // two-ended solve of Phi_bar in the FP64 / FP32 sweeps (option)
+  bool twisted_ready = false;     // reversed factor and interface inverses allocated (n = 4, K >= 4)
+  float* fac_rev32 = nullptr;     // FP32 copies of the reversed factor and the interface inverses
+  float* sinv32 = nullptr;
   int* fault = nullptr;           // device word set when a bounded wait inside a sweep ran out
   int kappa = 0;             // record the PCG coefficients and estimate the condition number
   double* hist = nullptr;    // device: vartheta_j, beta_j pairs
@@ -245,6 +250,16 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   const long long fac_rec = 24LL * n * n;
   const long long fac_vc = fac_rec * K;
   ALLOC(sb.fac, (size_t)g.V * 2 * fac_vc);
+  if (n == 4 && K >= kTwistedMinK) {
+    // the tiled sweeps (FP64, and FP32 below the bulk-copy kernel's grid
+    // size) solve Phi_bar from both ends by default: half the dependent
+    // chain per (column pair, time) block, twice the warps
+    ALLOC(sb.fac_rev, (size_t)g.V * 2 * fac_vc);
+    ALLOC(sb.iface, (size_t)g.V * 2 * 9 * (size_t)(4 * nn));
+    ALLOC(sb.sinv, (size_t)g.V * 2 * 4 * (size_t)(4 * nn));
+    h->twisted[0] = h->twisted[1] = 1;
+    h->twisted_ready = true;  // filled by the setup that follows allocation
+  }
   const size_t vec = (size_t)g.Ps * n;
   ALLOC(h->rhs, vec);
   ALLOC(h->delta, vec);
@@ -322,6 +337,11 @@ void convert_prec_f32(lq2d_problem* h, cudaStream_t s) {
     launch_t0_records(h->g, h->pd32.Qm, const_cast<float*>(h->pd32.fac_t0), h->nd.fac_rec, s);
     h->launches += 1;
   }
+  if (h->fac_rev32) {
+    launch_to_f32(h->sb.fac_rev, h->fac_rev32, (long long)h->g.V * 2 * h->nd.fac_vc, s);
+    launch_to_f32(h->sb.sinv, h->sinv32, (long long)h->g.V * 2 * 16LL * h->g.n * h->g.n, s);
+    h->launches += 2;
+  }
 }
 
 // Setup on `s`: inverses, splitting blocks, factors, right-hand side and its
@@ -376,6 +396,27 @@ int create_common(lq2d_problem** out, int K, int N, int T, int n, int m, const d
   }
   *out = h;
   return LQ2D_OK;
+}
+
+// Preconditioner data of the FP64 / FP32 sweeps: with the two-ended solve
+// enabled for that precision (and set up), the reversed factor and the
+// interface inverses ride along, which selects the two-ended kernels; the
+// n = 4 FP32 bulk-copy schedules (steps >= 1) are one-sided.
+PrecData<double> prec64(const lq2d_problem* h) {
+  PrecData<double> p = h->pd64;
+  if (h->twisted[0] && h->twisted_ready) {
+    p.fac_rev = h->sb.fac_rev;
+    p.sinv = h->sb.sinv;
+  }
+  return p;
+}
+PrecData<float> prec32(const lq2d_problem* h) {
+  PrecData<float> p = h->pd32;
+  if (h->twisted[1] && h->twisted_ready && h->fac_rev32 && !(h->g.n == 4 && h->sweep_steps >= 1)) {
+    p.fac_rev = h->fac_rev32;
+    p.sinv = h->sinv32;
+  }
+  return p;
 }
 
 // The S x L sweeps of one preconditioner application q = D_S r_in
@@ -448,9 +489,9 @@ const void* enqueue_precond_t(lq2d_problem* h, int S, int L, bool fuse_update, b
       cudaEventRecord(e0, s);
     }
     if constexpr (sizeof(VT) == 4)
-      h->kt->sweep_f32(e.variant, h->sweep_threads[1], h->sweep_steps, h->g, h->pd32, e.a, st, s);
+      h->kt->sweep_f32(e.variant, h->sweep_threads[1], h->sweep_steps, h->g, prec32(h), e.a, st, s);
     else
-      h->kt->sweep(e.variant, h->sweep_threads[0], h->g, h->pd64, e.a, st, s);
+      h->kt->sweep(e.variant, h->sweep_threads[0], h->g, prec64(h), e.a, st, s);
     h->launches += 1;
     if (timing) cudaEventRecord(e1, s);
   }
@@ -535,15 +576,20 @@ void enqueue_step(lq2d_problem* h, int S, int L, cudaStream_t s, bool timing) {
   }
 }
 
-// CTA width of the sweeps the current precision mode launches.
+// CTA width of the sweeps the current precision mode launches, and the rest
+// of its schedule (time steps per lane of the n = 4 FP32 sweeps, two-ended
+// solve), which captured graphs depend on.
 int current_threads(const lq2d_problem* h) { return h->sweep_threads[h->precision >= 1 ? 1 : 0]; }
+int current_steps(const lq2d_problem* h) { return h->precision >= 1 ? h->sweep_steps : 0; }
+int current_twisted(const lq2d_problem* h) { return h->twisted[h->precision >= 1 ? 1 : 0] && h->twisted_ready; }
 
 int sweeps_per_step(const lq2d_problem* h, int S, int L) { return h->precond_kind == 1 ? 1 : S * L; }
 
 int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   for (int i = 0; i < h->ngraphs; ++i)
     if (h->graphs[i].S == S && h->graphs[i].L == L && h->graphs[i].precision == h->precision &&
-        h->graphs[i].precond == h->precond_kind && h->graphs[i].threads == current_threads(h)) {
+        h->graphs[i].precond == h->precond_kind && h->graphs[i].threads == current_threads(h) &&
+        h->graphs[i].steps == current_steps(h) && h->graphs[i].twisted == current_twisted(h)) {
       *exec = h->graphs[i].exec;
       return LQ2D_OK;
     }
@@ -559,6 +605,8 @@ int get_graph(lq2d_problem* h, int S, int L, cudaGraphExec_t* exec) {
   ge.precision = h->precision;
   ge.precond = h->precond_kind;
   ge.threads = current_threads(h);
+  ge.steps = current_steps(h);
+  ge.twisted = current_twisted(h);
   LQ_CUDA(cudaGraphCreate(&ge.graph, 0));
   cudaGraphConditionalHandle hc;
   LQ_CUDA(cudaGraphConditionalHandleCreate(&hc, ge.graph, 1u, cudaGraphCondAssignDefault));
@@ -886,9 +934,9 @@ void enqueue_nbjm_outer(lq2d_problem* h, int L, int step, cudaStream_t s) {
       a.theta_in = prev;
     }
     if constexpr (sizeof(VT) == 4)
-      h->kt->sweep_f32(variant, h->sweep_threads[1], h->sweep_steps, h->g, h->pd32, a, h->st, s);
+      h->kt->sweep_f32(variant, h->sweep_threads[1], h->sweep_steps, h->g, prec32(h), a, h->st, s);
     else
-      h->kt->sweep(variant, h->sweep_threads[0], h->g, h->pd64, a, h->st, s);
+      h->kt->sweep(variant, h->sweep_threads[0], h->g, prec64(h), a, h->st, s);
     prev = B[others[l & 1]];
   }
   launch_nbjm_diff(h->g, prev, cur < 0 ? nullptr : B[cur], sizeof(VT) == 4, h->partials, h->st, s);
@@ -993,7 +1041,8 @@ void enqueue_solve_finish(lq2d_problem* h, double* slot, cudaStream_t s) {
 
 // The per-problem settings a captured batch graph depends on.
 int batch_mode_key(const lq2d_problem* h) {
-  return ((current_threads(h) * 4 + h->precision) * 4 + h->precond_kind) * 4 + h->stop_mode;
+  const int sched = (current_threads(h) * 8 + current_steps(h)) * 2 + current_twisted(h);
+  return ((sched * 4 + h->precision) * 4 + h->precond_kind) * 4 + h->stop_mode;
 }
 
 // The persistent batched loop serves FP64 NBJM problems with n = 4, S x L
@@ -1187,6 +1236,8 @@ int batch_build(lq2d_batch* b, double tol, int S, int L, int max_iter) {
   return LQ2D_OK;
 }
 
+int ensure_twisted_f32(lq2d_problem* h, cudaStream_t s);
+
 // FP32 copies of the preconditioner's operands and of the Delta product's
 // blocks (precision modes 1 and 2, and the multi-right-hand-side solve),
 // allocated on first use and refreshed at every setup.
@@ -1229,7 +1280,7 @@ int ensure_f32(lq2d_problem* h) {
     LQ_CUDA(cudaStreamSynchronize(nullptr));
     LQ_CUDA(cudaGetLastError());
   }
-  return LQ2D_OK;
+  return ensure_twisted_f32(h, nullptr);
 }
 
 // Float buffer of `count` elements from the handle's allocations.
@@ -1238,6 +1289,21 @@ int alloc_floats(lq2d_problem* h, float** p, size_t count) {
   const int rc = dev_alloc(h, &d, (count + 1) / 2);
   *p = reinterpret_cast<float*>(d);
   return rc;
+}
+
+// FP32 copies of the two-ended solve's arrays (when both the FP32 operands
+// and the two-ended setup exist); converted at every setup.
+int ensure_twisted_f32(lq2d_problem* h, cudaStream_t s) {
+  if (h->fac_rev32 || !h->twisted_ready || !h->f32_buf) return LQ2D_OK;
+  const Grid& g = h->g;
+  int rc;
+  if ((rc = alloc_floats(h, &h->fac_rev32, (size_t)g.V * 2 * h->nd.fac_vc)) != LQ2D_OK) return rc;
+  if ((rc = alloc_floats(h, &h->sinv32, (size_t)g.V * 2 * 16 * g.n * g.n)) != LQ2D_OK) return rc;
+  launch_to_f32(h->sb.fac_rev, h->fac_rev32, (long long)g.V * 2 * h->nd.fac_vc, s);
+  launch_to_f32(h->sb.sinv, h->sinv32, (long long)g.V * 2 * 16LL * g.n * g.n, s);
+  h->launches += 2;
+  LQ_CUDA(cudaStreamSynchronize(s));
+  return LQ2D_OK;
 }
 
 // Multi-right-hand-side operands: allocated on first use, rebuilt from the
@@ -1685,19 +1751,28 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
     cudaEventDestroy(e0);
     return fail(LQ2D_ECUDA, "cudaEventCreate failed");
   }
-  // candidates: CTA widths, and for the n = 4 FP32 sweeps the compiled
-  // (width, time steps per lane) schedules
-  int cand[12][2] = {{32, 1}, {64, 1}, {128, 1}, {256, 1}};
-  int ncand = 4;
+  // candidates (width, time steps per lane, two-ended): the CTA widths, for
+  // the n = 4 FP32 sweeps the compiled (width, steps) schedules, and the
+  // two-ended solve where it applies (n = 4, K >= 4, tiled widths 32, 64)
+  int sched[12][2] = {{32, 0}, {64, 0}, {128, 0}, {256, 0}};
+  int nsched = 4;
   const bool bulk = slot == 1 && g.n == 4;
-  if (bulk) ncand = sweep4_f32_configs(cand, 12);
-  const int saved_steps = h->sweep_steps;
+  if (bulk) nsched = sweep4_f32_configs(sched, 12);
+  const bool tw_ok = h->twisted_ready;
+  std::vector<std::array<int, 3>> cand;
+  for (int c = 0; c < nsched; ++c) {
+    cand.push_back({sched[c][0], sched[c][1], 0});
+    if (tw_ok && sched[c][1] == 0 && (sched[c][0] == 32 || sched[c][0] == 64))
+      cand.push_back({sched[c][0], sched[c][1], 1});
+  }
+  const int saved_steps = h->sweep_steps, saved_tw = h->twisted[slot];
   double best_ms = 0.0;
-  int best = saved, best_steps = saved_steps;
+  int best = saved, best_steps = saved_steps, best_tw = saved_tw;
   cudaError_t err = cudaSuccess;
-  for (int c = 0; c < ncand && err == cudaSuccess; ++c) {
+  for (size_t c = 0; c < cand.size() && err == cudaSuccess; ++c) {
     h->sweep_threads[slot] = cand[c][0];
     if (bulk) h->sweep_steps = cand[c][1];
+    h->twisted[slot] = cand[c][2];
     enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);  // warm-up
     cudaEventRecord(e0, s);
     for (int r = 0; r < reps; ++r) enqueue_precond(h, S, L, false, false, nullptr, h->y, s, false);
@@ -1710,6 +1785,7 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
       best_ms = per;
       best = cand[c][0];
       best_steps = bulk ? cand[c][1] : saved_steps;
+      best_tw = cand[c][2];
     }
   }
   cudaEventDestroy(e0);
@@ -1718,10 +1794,12 @@ int lq2d_autotune(lq2d_problem* h, int S, int L, int reps, int* threads, double*
   if (err != cudaSuccess) {
     h->sweep_threads[slot] = saved;
     h->sweep_steps = saved_steps;
+    h->twisted[slot] = saved_tw;
     return fail(LQ2D_ECUDA, cudaGetErrorString(err));
   }
   h->sweep_threads[slot] = best;
   h->sweep_steps = best_steps;
+  h->twisted[slot] = best_tw;
   if (threads) *threads = best;
   if (ms) *ms = best_ms;
   return LQ2D_OK;
@@ -1970,8 +2048,34 @@ int lq2d_set_option(lq2d_problem* h, int option, double value) {
       if (v != 0 && v != 1 && v != 2 && v != 4) return fail(LQ2D_EINVAL, "sweep steps must be 0, 1, 2 or 4");
       h->sweep_steps = v;
       return LQ2D_OK;
+    case LQ2D_OPT_TWISTED:
+      if (v != 0 && v != 1) return fail(LQ2D_EINVAL, "twisted must be 0 or 1");
+      h->twisted[0] = h->twisted[1] = v;
+      return LQ2D_OK;
     default:
       return fail(LQ2D_EINVAL, "unknown option");
+  }
+}
+
+int lq2d_get_option(const lq2d_problem* h, int option, double* value) {
+  if (!h || !value) return fail(LQ2D_EINVAL, "null argument");
+  const int slot = h->precision >= 1 ? 1 : 0;
+  switch (option) {
+    case LQ2D_OPT_STOP_MODE: *value = h->stop_mode; return LQ2D_OK;
+    case LQ2D_OPT_DRIVER: *value = h->driver; return LQ2D_OK;
+    case LQ2D_OPT_TIMING: *value = h->timing; return LQ2D_OK;
+    case LQ2D_OPT_MAX_RESTARTS: *value = h->max_restarts; return LQ2D_OK;
+    case LQ2D_OPT_PRECONDITIONER: *value = h->precond_kind; return LQ2D_OK;
+    case LQ2D_OPT_KAPPA: *value = h->kappa; return LQ2D_OK;
+    case LQ2D_OPT_SWEEP_THREADS: *value = h->sweep_threads[slot]; return LQ2D_OK;
+    case LQ2D_OPT_SWEEP_STEPS: *value = h->sweep_steps; return LQ2D_OK;
+    case LQ2D_OPT_TWISTED: {  // widths above 64 and the bulk-copy FP32 schedules solve one-ended
+      const int thr = h->sweep_threads[slot];
+      *value = (current_twisted(h) && (thr == 32 || thr == 64) &&
+                !(slot == 1 && h->g.n == 4 && h->sweep_steps >= 1)) ? 1 : 0;
+      return LQ2D_OK;
+    }
+    default: return fail(LQ2D_EINVAL, "unknown option");
   }
 }
 

@@ -27,7 +27,17 @@ struct SetupBuffers {
   double* M13;
   double* Om;
   double* fac;
+  // two-ended (twisted) solve of Phi_bar, when enabled: the factor of the
+  // reversed pair-row order, the interface blocks and the inverted interface
+  // Schur complement per (v, class); NULL otherwise
+  double* fac_rev;
+  double* iface;
+  double* sinv;
 };
+
+// pair-rows from which the two-ended solve applies (top and bottom halves
+// of at least one row each around the two interface rows)
+constexpr int kTwistedMinK = 4;
 
 void launch_setup(const SetupBuffers& sb, int K, int N, int n, int m, int V, long long fac_rec,
                   long long fac_vc, int* d_status, cudaStream_t s);

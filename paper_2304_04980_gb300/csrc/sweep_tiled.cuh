@@ -131,10 +131,10 @@ __device__ __forceinline__ int h_of_dir(int jj, int dir) {
   return dir == 0 ? 1 : dir == 1 ? 0 : dir == 2 ? 7 : dir == 3 ? 4 : 5;
 }
 
-template <int NS, typename VT, int THR>
+template <int NS, typename VT, int THR, int NBUF = sweep_stages<VT>()>
 struct SweepSmem {
   using Geo = SweepGeom<NS, THR>;
-  static constexpr int NB = sweep_stages<VT>();
+  static constexpr int NB = NBUF;
   VT fac[NB][2][3 * Geo::BS];         // [buffer][class][3 blocks]
   VT halo[NB][Geo::NH][Geo::HW][NS];  // [buffer][h][t window][k]
   VT blk[NB][2][10][NS * NS];         // [buffer][jj][block][n x n]
@@ -143,6 +143,25 @@ struct SweepSmem {
   double src[NB][4][2][NS][Geo::TT];  // [buffer][r, y, d, delta or src][jj][k][t]; backward: r, y
   VT ys[NB][2][NS][Geo::TT];          // backward: forward result y of the pair-row
   alignas(16) VT qb[NB][2][NS * NS];  // Q of the pair-row's nodes (tiles holding t = 0)
+};
+
+// Staging buffers of the two-ended (twisted) solve.  Its CTAs hold two
+// halves' staging areas; in FP64 three buffers each would leave room for
+// half as many CTAs per SM, which on grids of few (column pair, time) blocks
+// costs a second wave, and one pair-row in flight covers the load latency
+// of its long FP64 steps.  The shorter FP32 steps keep two in flight.
+template <typename VT>
+__host__ __device__ constexpr int twisted_stages() { return sizeof(VT) == 8 ? 2 : 3; }
+
+// Shared memory of the interface step of the two-ended solve, after the two
+// halves' staging areas: the exchanges between the halves.  (The interface
+// couplings and S^-1 are read once per lane, straight from global memory.)
+template <int NS, typename VT, int THR>
+struct TwistSmem {
+  using Geo = SweepGeom<NS, THR>;
+  VT xch[2][Geo::TT][Geo::G2];     // each half's y two rows before the interface
+  VT rhs[Geo::TT][2 * Geo::G2];    // right-hand side of the interface solve
+  VT xs[Geo::TT][2 * Geo::G2];     // x_k, x_{k+1}
 };
 
 // Register budget of the sweeps: one CTA per SM fewer than the shared-memory
@@ -159,7 +178,15 @@ constexpr int sweep_min_blocks() {
 // The sweep for work unit `bid` of `nblocks` (one CTA's tile: column pair
 // bid / tiles, time steps from (bid % tiles) * TT); the kernel below runs one
 // unit per CTA, the batched persistent kernel many per CTA.
-template <int NS, int VAR, typename VT, int THR>
+//
+// TW: the two-ended (twisted) solve of each Phi_bar_{v,t}.  The CTA holds
+// two halves of THR threads: the top half eliminates pair-rows 0..k with the
+// forward factor, the bottom half pair-rows K-1..k+1 with the factor of the
+// reversed order (k = (K-2)/2), each with the staging and step of the
+// one-sided sweep; then both halves solve the interface rows k, k+1 with
+// S^-1 and run their backward substitutions away from it (rows k-1..0 and
+// k+2..K-1).  Half the dependent chain, twice the warps per (v, t).
+template <int NS, int VAR, typename VT, int THR, bool TW = false>
 __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT>& pd, const SweepArgsT<VT>& a,
                                                 SolverState* st, int bid, int nblocks) {
   // VT = float is the mixed mode: FP32 factors, blocks and iterates, with
@@ -173,7 +200,23 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   using Geo = SweepGeom<NS, THR>;
   constexpr int G2 = Geo::G2, GS = Geo::GS, BS = Geo::BS, TT = Geo::TT, HW = Geo::HW;
   extern __shared__ __align__(16) unsigned char sweep_smem[];
-  SweepSmem<NS, VT, THR>& sm = *reinterpret_cast<SweepSmem<NS, VT, THR>*>(sweep_smem);
+  constexpr int NB = TW ? twisted_stages<VT>() : sweep_stages<VT>();
+  constexpr int PD = NB - 1;  // prefetch distance in pair-rows
+  using Smem = SweepSmem<NS, VT, THR, NB>;
+  const int half = TW ? (int)(threadIdx.x / THR) : 0;  // 0: top (or one-sided), 1: bottom
+  Smem& sm = reinterpret_cast<Smem*>(sweep_smem)[half];
+  TwistSmem<NS, VT, THR>& tw = *reinterpret_cast<TwistSmem<NS, VT, THR>*>(sweep_smem + 2 * sizeof(Smem));
+  const int K = g.K;
+  const int kI = TW ? (K - 2) / 2 : 0;                                // interface rows kI, kI + 1
+  const int nf = TW ? (half ? K - kI - 1 : kI + 1) : K;               // forward steps of this half
+  const int nb = TW ? (half ? K - kI - 2 : kI) : K;                   // backward steps of this half
+  const int nf_all = TW ? (kI + 1 > K - kI - 1 ? kI + 1 : K - kI - 1) : K;
+  const int nb_all = TW ? (kI > K - kI - 2 ? kI : K - kI - 2) : K;
+  // physical pair-row of forward step s and of backward step s, and the
+  // record of the half's factor that backward step s reads
+  auto row_f = [&](int s) { return half ? K - 1 - s : s; };
+  auto row_b = [&](int s) { return TW ? (half ? kI + 2 + s : kI - 1 - s) : K - 1 - s; };
+  auto rec_b = [&](int s) { return half ? K - 1 - row_b(s) : row_b(s); };
 
   if (st != nullptr && st->done) return;
   const int Tp = g.T + 1;
@@ -183,7 +226,7 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   const int j0 = 2 * v;
   const bool two_cols = j0 + 1 < g.N;
   const bool has_last = t0 + TT > g.T;  // the tile holds t = T (class 1)
-  const int tid = threadIdx.x;
+  const int tid = TW ? (int)(threadIdx.x % THR) : (int)threadIdx.x;
   const int lane32 = tid & 31;
   const int al = tid & (GS - 1);
   const int grp = tid / GS;
@@ -204,7 +247,7 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   const int my_slot = has_last ? cls : 0;  // tiles without t = T stage class 0 only, at slot 0
   const double vth = UPDATE ? st->theta : 0.0;
   const bool flex_dot = FLEX && MU && st->have_mu;
-  const VT* fac_pair = pd.fac + (size_t)(2 * v) * pd.fac_vc;  // class c at fac_pair + c * fac_vc
+  const VT* fac_pair = (half ? pd.fac_rev : pd.fac) + (size_t)(2 * v) * pd.fac_vc;  // class c at + c * fac_vc
   const int ncls = has_last ? 2 : 1;
   constexpr int CH = 16 / sizeof(VT);  // elements per 16-byte copy
   double acc0 = 0.0, acc1 = 0.0;
@@ -358,9 +401,10 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   // ---- staging of the forward step for pair-row i into buffer b: F2, F1
   // of pair-row i per class, Q of its nodes (tiles holding t = 0), its own
   // entries, the neighbours' halo and the node blocks
-  auto stage_forward = [&](int i, int b) {
+  auto stage_forward = [&](int step, int b) {
+    const int i = row_f(step);  // physical pair-row; the record is the half's step
     const long long rb = (long long)i * row_stride;
-    const long long fo = (long long)i * pd.fac_rec;
+    const long long fo = (long long)step * pd.fac_rec;
 #pragma unroll
     for (int sl = 0; sl < FSL; ++sl)
       if ((f_ok >> sl) & 1u) cp_async_16(&sm.fac[b][0][0] + f_sm[sl], f_ptr[sl] + fo);
@@ -392,8 +436,9 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
 
   // ---- staging of the backward step for pair-row i: N2, N1 and D^-1 of
   // pair-row i, y_i of the tile and, in the mu sweep, r (and y)
-  auto stage_backward = [&](int i, int b) {
-    const long long fo = (long long)i * pd.fac_rec;
+  auto stage_backward = [&](int step, int b) {
+    const int i = row_b(step);
+    const long long fo = (long long)rec_b(step) * pd.fac_rec;
 #pragma unroll
     for (int sl = 0; sl < FSLB; ++sl)
       if ((fb_ok >> sl) & 1u) cp_async_16(&sm.fac[b][0][0] + (tid + sl * THR) * CH, fb_ptr[sl] + fo);
@@ -411,27 +456,29 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   VT ym1[G2], ym2[G2];
 #pragma unroll
   for (int bb = 0; bb < G2; ++bb) { ym1[bb] = VT(0); ym2[bb] = VT(0); }
+  VT y_last = VT(0);  // the lane's own result of the half's last forward step
 
-  constexpr int NB = sweep_stages<VT>();
-  constexpr int PD = NB - 1;  // prefetch distance in pair-rows
   // one commit group per pair-row (empty past the last one), so that the
   // wait below counts pair-rows
 #pragma unroll
   for (int s0 = 0; s0 < PD; ++s0) {
-    if (s0 < g.K) stage_forward(s0, s0);
+    if (s0 < nf) stage_forward(s0, s0);
     cp_async_commit();
   }
-  for (int i = 0; i < g.K; ++i) {
-    const int b = i % NB;
+  for (int fs = 0; fs < nf_all; ++fs) {
+    const int b = fs % NB;
+    const int i = row_f(fs);
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
-    // pair-row i has landed (rows i+1 .. i+PD-1 may be in flight); after the
-    // barrier every thread is done with step i-1, whose buffer takes
-    // pair-row i+PD
+    // step fs has landed (steps fs+1 .. fs+PD-1 may be in flight); after the
+    // barrier every thread is done with step fs-1, whose buffer takes step
+    // fs+PD.  A half with fewer steps (two-ended solve, K odd) idles through
+    // the last one.
     cp_async_wait<PD - 1>();
     __syncthreads();
-    if (i + PD < g.K) stage_forward(i + PD, (i + PD) % NB);
+    if (fs + PD < nf) stage_forward(fs + PD, (fs + PD) % NB);
     cp_async_commit();
+    if (fs >= nf) continue;
     const unsigned valid = HALO ? row_valid(i) : 0u;
     VT tau = VT(0);
     if (node_ok) {
@@ -508,25 +555,27 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
         out += Qrow[c] * tc;
       }
       if (node_ok) a.theta_out[it_idx(k, off)] = out;
+      y_last = out;
     } else {
       // y_i = tau_i - F2 y_{i-2} - F1 y_{i-1}, one chain of multiply-adds
       // (the FP64 pipe's issue rate, not its latency, bounds the sweep, so
       // no partial sums are split off)
       const VT* rec = sm.fac[b][my_slot];  // [F2][F1], row-major
       VT yv = tau;
-      if (i >= 2) {
+      if (fs >= 2) {
         VT row[G2];
         lds_run<VT, G2>(rec + ac * G2, row);
 #pragma unroll
         for (int bb = 0; bb < G2; ++bb) yv -= row[bb] * ym2[bb];
       }
-      if (i >= 1) {
+      if (fs >= 1) {
         VT row[G2];
         lds_run<VT, G2>(rec + BS + ac * G2, row);
 #pragma unroll
         for (int bb = 0; bb < G2; ++bb) yv -= row[bb] * ym1[bb];
       }
       if (node_ok) a.theta_out[it_idx(k, off)] = yv;
+      y_last = yv;
       if (lane_ok) sm.xy[grp][al] = yv;
       __syncwarp(gmask);
 #pragma unroll
@@ -537,24 +586,76 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   cp_async_wait<0>();
   __syncthreads();
 
-  // ---- backward substitution
   VT xp1[G2], xp2[G2];
 #pragma unroll
   for (int bb = 0; bb < G2; ++bb) { xp1[bb] = VT(0); xp2[bb] = VT(0); }
+
+  // ---- interface of the two-ended solve, rows k and k+1:
+  //   [x_k; x_{k+1}] = S^-1 [y_k - J w_{k+2}; w_{k+1} - H y_{k-1}]
+  // (y: top half's forward results, w: bottom half's), which seeds both
+  // backward substitutions
+  if constexpr (TW) {
+    // the lane's rows of the coupling (top: J, the reversed factor's F2 of
+    // row k; bottom: H, the forward factor's F2 of row k+1) and of S^-1
+    const VT* Cm = half ? pd.fac + (size_t)(2 * v + cls) * pd.fac_vc + (size_t)(kI + 1) * pd.fac_rec
+                        : pd.fac_rev + (size_t)(2 * v + cls) * pd.fac_vc + (size_t)(K - kI - 1) * pd.fac_rec;
+    Cm += 3 * BS + ac * G2;
+    const VT* Srow = pd.sinv + (size_t)(2 * v + cls) * 4 * BS + (half * G2 + ac) * 2 * G2;
+    if (active && al == 0) {
+#pragma unroll
+      for (int bb = 0; bb < G2; ++bb) tw.xch[half][grp][bb] = ym2[bb];
+    }
+    __syncthreads();
+    if (active && lane_ok && t >= 1) {
+      VT rr = y_last;
+#pragma unroll
+      for (int bb = 0; bb < G2; ++bb) rr -= Cm[bb] * tw.xch[half ^ 1][grp][bb];
+      tw.rhs[grp][half * G2 + al] = rr;
+    }
+    __syncthreads();
+    if (active && lane_ok) {
+      const long long offI = ((long long)(kI + half) * g.N + j) * Tp + t;
+      VT xv = y_last;  // t = 0: theta_0 = Q tau_0 is final after the forward pass
+      if (t >= 1) {
+        xv = VT(0);
+#pragma unroll
+        for (int c = 0; c < 2 * G2; ++c) xv += Srow[c] * tw.rhs[grp][c];
+        if (node_ok) a.theta_out[it_idx(k, offI)] = xv;
+      }
+      if (node_ok) {
+        if (MU) acc0 += (double)xv * a.r[kP + offI];
+        if (flex_dot) acc1 += (double)xv * a.y[kP + offI];
+      }
+      tw.xs[grp][half * G2 + al] = xv;
+    }
+    __syncthreads();
+    if (active) {
+      // top: x_{i+1} = x_k, x_{i+2} = x_{k+1}; bottom: x_{i-1} = x_{k+1}, x_{i-2} = x_k
+#pragma unroll
+      for (int bb = 0; bb < G2; ++bb) {
+        xp1[bb] = tw.xs[grp][half * G2 + bb];
+        xp2[bb] = tw.xs[grp][(half ^ 1) * G2 + bb];
+      }
+    }
+  }
+
+  // ---- backward substitution (one-sided: pair-rows K-1..0; two-ended: each
+  // half from the interface outwards)
 #pragma unroll
   for (int s0 = 0; s0 < PD; ++s0) {
-    if (s0 < g.K) stage_backward(g.K - 1 - s0, s0);
+    if (s0 < nb) stage_backward(s0, s0);
     cp_async_commit();
   }
-  for (int i = g.K - 1; i >= 0; --i) {
-    const int step = g.K - 1 - i;
-    const int b = step % NB;
+  for (int bstep = 0; bstep < nb_all; ++bstep) {
+    const int i = row_b(bstep);
+    const int b = bstep % NB;
     const int p = i * g.N + j;
     const long long off = node_ok ? (long long)p * Tp + t : 0;
     cp_async_wait<PD - 1>();
     __syncthreads();
-    if (i >= PD) stage_backward(i - PD, (step + PD) % NB);
+    if (bstep + PD < nb) stage_backward(bstep + PD, (bstep + PD) % NB);
     cp_async_commit();
+    if (bstep >= nb) continue;
     VT yown = VT(0);
     double r_own = 0.0, y_own = 0.0;
     if (node_ok) {
@@ -578,13 +679,13 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
       VT xv = VT(0);
 #pragma unroll
       for (int bb = 0; bb < G2; ++bb) xv += row0[bb] * yall[bb];
-      if (i + 2 < g.K) {
+      if (TW || i + 2 < g.K) {
         VT row[G2];
         lds_run<VT, G2>(rec + ac * G2, row);
 #pragma unroll
         for (int bb = 0; bb < G2; ++bb) xv -= row[bb] * xp2[bb];
       }
-      if (i + 1 < g.K) {
+      if (TW || i + 1 < g.K) {
         VT row[G2];
         lds_run<VT, G2>(rec + BS + ac * G2, row);
 #pragma unroll
@@ -649,8 +750,30 @@ __global__ void __launch_bounds__(THR, (sweep_min_blocks<NS, VT, THR>()))
   nbjm_sweep_body<NS, VAR, VT, THR>(g, pd, a, st, blockIdx.x, gridDim.x);
 }
 
+// The two-ended solve: CTAs of 2 THR threads (two halves).
+template <int NS, typename VT, int THR>
+constexpr size_t sweep_twisted_smem_bytes() {
+  return 2 * sizeof(SweepSmem<NS, VT, THR, twisted_stages<VT>()>) + sizeof(TwistSmem<NS, VT, THR>);
+}
+
+// CTAs per SM the two-ended sweep's shared memory allows (at most 8)
+template <int NS, typename VT, int THR>
+constexpr int sweep_twisted_min_blocks() {
+  constexpr int by_smem = 232448 / ((int)sweep_twisted_smem_bytes<NS, VT, THR>() + 1024);
+  constexpr int by_threads = 2048 / (2 * THR);
+  constexpr int b = by_smem < by_threads ? by_smem : by_threads;
+  return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
+template <int NS, int VAR, typename VT, int THR>
+__global__ void __launch_bounds__(2 * THR, (sweep_twisted_min_blocks<NS, VT, THR>()))
+    nbjm_sweep_twisted_kernel(Grid g, PrecData<VT> pd, SweepArgsT<VT> a, SolverState* st) {
+  nbjm_sweep_body<NS, VAR, VT, THR, true>(g, pd, a, st, blockIdx.x, gridDim.x);
+}
+
 template <int NS, typename VT, int THR>
 constexpr size_t sweep_smem_bytes() { return sizeof(SweepSmem<NS, VT, THR>); }
+
 
 template <int NS, int THR>
 inline unsigned sweep_blocks(const Grid& g) {

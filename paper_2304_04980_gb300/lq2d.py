@@ -20,7 +20,7 @@ OK, EINVAL, ENOTPD, ENOCONV, EBREAKDOWN, ECUDA, ENOMEM, ETIMEOUT = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ECUDA",
                 6: "ENOMEM", 7: "ETIMEOUT"}
 OPT_STOP_MODE, OPT_DRIVER, OPT_TIMING, OPT_MAX_RESTARTS, OPT_PRECONDITIONER, OPT_KAPPA = 1, 2, 3, 4, 5, 6
-OPT_SWEEP_THREADS, OPT_SWEEP_STEPS = 7, 8
+OPT_SWEEP_THREADS, OPT_SWEEP_STEPS, OPT_TWISTED = 7, 8, 9
 BATCH_PERSISTENT, BATCH_THREADS, BATCH_USES_PERSISTENT = 1, 2, 3
 
 EXPORTED = (
@@ -29,7 +29,7 @@ EXPORTED = (
     "lq2d_apply_precond_multi_device", "lq2d_solve_multi_device",
     "lq2d_autotune",
     "lq2d_batch_create", "lq2d_batch_solve", "lq2d_batch_destroy", "lq2d_get_solution_device",
-    "lq2d_batch_set_option", "lq2d_batch_get_option", "lq2d_batch_autotune",
+    "lq2d_batch_set_option", "lq2d_batch_get_option", "lq2d_batch_autotune", "lq2d_get_option",
     "lq2d_set_option",
     "lq2d_get_stats", "lq2d_set_precision", "lq2d_destroy", "lq2d_last_error",
     "lq2d_wsnet_create", "lq2d_wsnet_param_count", "lq2d_wsnet_set_params", "lq2d_wsnet_get_params",
@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         "lq2d_batch_autotune": (i, [_vp, i, i, i, _ip, _dp, _vp]),
         "lq2d_get_solution_device": (i, [_vp, _vp, _vp, _vp, _vp]),
         "lq2d_set_option": (i, [_vp, i, d]),
+        "lq2d_get_option": (i, [_vp, i, _dp]),
         "lq2d_get_stats": (i, [_vp, ctypes.POINTER(Stats)]),
         "lq2d_set_precision": (i, [_vp, i]),
         "lq2d_destroy": (None, [_vp]),
@@ -284,6 +285,11 @@ class Problem:
 
     def set_option(self, option, value):
         _check(load().lq2d_set_option(self._h, option, float(value)))
+
+    def get_option(self, option):
+        v = ctypes.c_double(0.0)
+        _check(load().lq2d_get_option(self._h, option, ctypes.byref(v)))
+        return v.value
 
     def stats(self) -> dict:
         s = Stats()

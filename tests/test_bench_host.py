@@ -54,6 +54,22 @@ def test_profiled_traffic_requires_the_current_kernel_hash(tmp_path, monkeypatch
     assert bench.profiled_traffic("w", "fp32") is None
 
 
+def test_profiled_traffic_requires_the_same_kernel(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda precision="fp64": "abcdef0123456789")
+    one = bench.sweep_kernel_name({"threads": 64, "steps_per_lane": 0, "two_ended": 0}, "double")
+    two = bench.sweep_kernel_name({"threads": 64, "steps_per_lane": 0, "two_ended": 1}, "double")
+    bulk = bench.sweep_kernel_name({"threads": 128, "steps_per_lane": 2, "two_ended": 1}, "float")
+    assert len({one, two, bulk}) == 3 and "twisted" in two and "bulk" in bulk
+    (prof / "nbjm_sweep_w.md").write_text("kernel source hash: abcdef0123456789\nprofiled kernel: %s\n"
+                                          "dram bytes per launch (read+write): 42\n" % one)
+    assert bench.profiled_traffic("w", "fp64", one) == 42.0
+    assert bench.profiled_traffic("w", "fp64", two) is None
+    assert bench.profiled_traffic("w", "fp64") == 42.0
+
+
 def test_kernel_hash_covers_the_sweep_sources():
     for precision in ("fp64", "fp32"):
         h = bench.kernel_source_hash(precision)

@@ -40,6 +40,8 @@ def test_batch_equals_single_solves_and_oracle(dev):
     lq2d = lq()
     grids = small_batch()
     probs = [lq2d.Problem.from_grid(g) for g in grids]
+    for p in probs:  # the persistent loop's sweeps are one-sided
+        p.set_option(lq2d.OPT_TWISTED, 0)
     batch = lq2d.Batch(probs)
     out = batch.solve(1e-11, 2, 2, 5000)
     assert out["status"] == 0 and all(s == 0 for s in out["statuses"])
@@ -149,12 +151,15 @@ def test_autotune_picks_a_width_and_keeps_results(dev):
 def test_persistent_loop_equals_chains_single_solves_and_oracle(dev):
     """The persistent batched loop (one launch per kernel of a PCG step for
     every problem, work pulled from a device queue) gives each problem the
-    result of its own single solve with the same sweep width, bit for bit,
-    and the one-chain-per-problem graph gives the same; uneven K, N, T (odd N,
-    K = 1, N = 1 included)."""
+    result of its own single solve with the same sweep width and one-sided
+    sweeps, bit for bit, and the one-chain-per-problem graph gives the same;
+    uneven K, N, T (odd N, K = 1, N = 1 included).  With the two-ended solve
+    (the single solves' default) the chains match the oracle."""
     lq2d = lq()
     grids = synth.batch_grids(12, seed=23, K_range=(1, 11), N_range=(1, 12), T_range=(1, 30))
     probs = [lq2d.Problem.from_grid(g) for g in grids]
+    for p in probs:
+        p.set_option(lq2d.OPT_TWISTED, 0)
     batch = lq2d.Batch(probs)
     for width in (32, 128, 64):
         batch.set_option(lq2d.BATCH_THREADS, width)
@@ -173,10 +178,15 @@ def test_persistent_loop_equals_chains_single_solves_and_oracle(dev):
     assert chains["iterations"] == out["iterations"]
     for p, g, lam in zip(probs, grids, persistent):
         assert np.array_equal(costate_of(p, g, dev), lam)
+    for p in probs:
+        p.set_option(lq2d.OPT_TWISTED, 1)
+    chains2 = batch.solve(1e-11, 2, 2, 5000)
+    assert chains2["status"] == 0
     for idx in (0, 5, len(grids) - 1):
         g = grids[idx]
         ref = O.Oracle(O.Problem.from_arrays(g.K, g.N, g.T, g.n, g.m, *g.arrays())).solve(1e-12)
         assert np.linalg.norm(persistent[idx] - ref.delta) <= 1e-8 * np.linalg.norm(ref.delta)
+        assert np.linalg.norm(costate_of(probs[idx], g, dev) - ref.delta) <= 1e-8 * np.linalg.norm(ref.delta)
     batch.close()
 
 
