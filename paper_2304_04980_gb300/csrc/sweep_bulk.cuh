@@ -129,8 +129,28 @@ struct Geo {
   static constexpr bool OMEGA = VAR == kSweepOmega || VAR == kSweepOmegaMu || VAR == kSweepXiOmega;
   static constexpr bool MU = VAR == kSweepOmegaMu;
   static constexpr int NV = UPDATE ? 4 : (MU ? 2 : 1);  // FP64 runs per (jj, k) in one buffer
-  static constexpr int RUN64 = TT + 4;                   // doubles per FP64 run slot (aligned superset)
+  static constexpr int RUN64 = TT + 2;                   // doubles per FP64 run slot (aligned superset)
+  // copies of a step, at most: 3 factor classes, then node blocks, 8
+  // neighbour windows and the pair-row's own runs (forward), or y_i and the
+  // mu runs (backward)
+  static constexpr int NFWD = UPDATE ? 3 + 4 * 8 : 3 + 2 + 8 + 8;
+  static constexpr int NBWD = MU ? 3 + 2 + 16 : 3 + 2;
 };
+
+constexpr int kMaxCopies = 48;  // bulk copies of one step, at most
+
+// One bulk copy of a pair-row step: a fixed run whose source advances by a
+// fixed stride per pair-row.
+struct CopyDesc {
+  const char* base;     // source at pair-row 0 (flagged windows: outside the array there)
+  unsigned stride8;     // 8-byte words per pair-row
+  unsigned short dst;   // byte offset inside a staging buffer
+  unsigned short info;  // bytes (bits 0..11) and the flags below
+};
+constexpr unsigned short kNeedAbove = 1u << 12;  // window of the row above: pair-rows 1..K-1
+constexpr unsigned short kNeedBelow = 1u << 13;  // window of the row below: pair-rows 0..K-2
+constexpr unsigned short kRun64 = 1u << 14;      // FP64 run, copied as its aligned 16-byte superset
+constexpr unsigned short kBytesMask = 0xfffu;
 
 template <int VAR, int R, int THR>
 struct Smem {
@@ -145,6 +165,9 @@ struct Smem {
   Buf buf[stages<R>()];
   float xy[G::NG][R][G2];                 // per group: the step's result, exchanged inside the group
   uint64_t bar[stages<R>()];
+  CopyDesc desc_f[G::NFWD];               // the CTA's copies per step: forward pass
+  CopyDesc desc_b[G::NBWD];               // backward pass
+  int ndesc[2];
 };
 
 // CTAs per SM to budget registers for: as many as shared memory allows.
@@ -155,8 +178,6 @@ constexpr int min_blocks() {
   constexpr int b = by_smem < by_threads ? by_smem : by_threads;
   return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
-
-constexpr int kMaxCopies = 48;  // bulk copies of one step, at most
 
 }  // namespace bulk
 
@@ -238,104 +259,149 @@ __global__ void __launch_bounds__(THR, (bulk::min_blocks<VAR, R, THR>()))
   }
   __syncthreads();
 
-  // ---- one bulk copy of a step: copy index c -> (source, destination, bytes);
-  // bytes = 0 when the copy does not exist for this tile or pair-row
-  auto fac_base = [&](int c) -> const float* {
-    return c == 2 ? pd.fac_t0 + (size_t)v * pd.fac_vc : pd.fac + (size_t)(2 * v + c) * pd.fac_vc;
+  // ---- the copies of a step, described once per CTA (thread 0): candidate
+  // copy c of a pass -> (source at pair-row 0, stride, place, bytes, flags),
+  // false when the copy does not exist for this tile
+  auto buf_off = [&](const void* q) -> unsigned short {
+    return (unsigned short)(reinterpret_cast<const char*>(q) - reinterpret_cast<const char*>(&sm.buf[0]));
   };
-  auto run64 = [&](const double* vec, int i, int cjj, int kk, const void** src) -> unsigned {
-    const long long e0 = kk * Ps + (long long)(i * N + j0 + cjj) * Tp + tl;
-    const long long a0 = e0 & ~1LL;
-    *src = vec + a0;
-    return (unsigned)(((e0 - a0 + ntl + 1) & ~1LL) * 8);
+  const unsigned row_iter8 = (unsigned)((long long)N * Tp * 2);  // 8-byte words per grid row of an FP32 iterate
+  auto run64 = [&](const double* vec, int cjj, int kk, CopyDesc& d) {
+    d.base = reinterpret_cast<const char*>(vec + kk * Ps + (long long)(j0 + cjj) * Tp + tl);
+    d.stride8 = (unsigned)((long long)N * Tp);
+    d.info = kRun64;
   };
-  auto decode = [&](int c, int i, bool fwd, int b, const void** src, void** dst) -> unsigned {
-    typename Sm::Buf& B = sm.buf[b];
+  auto describe = [&](int c, bool fwd, CopyDesc& d) -> bool {
+    typename Sm::Buf& B = sm.buf[0];
     if (c < 3) {
-      if (!((cls_mask >> c) & 1u)) return 0u;
-      *src = fac_base(c) + (size_t)i * pd.fac_rec + (fwd ? 3 * BS : 0);
-      *dst = &B.fac[c][0];
-      return fwd ? 2 * BS * 4 : 3 * BS * 4;
+      if (!((cls_mask >> c) & 1u)) return false;
+      const float* f = c == 2 ? pd.fac_t0 + (size_t)v * pd.fac_vc : pd.fac + (size_t)(2 * v + c) * pd.fac_vc;
+      d.base = reinterpret_cast<const char*>(f + (fwd ? 3 * BS : 0));
+      d.stride8 = (unsigned)(pd.fac_rec / 2);
+      d.dst = buf_off(&B.fac[c][0]);
+      d.info = (unsigned short)(fwd ? 2 * BS * 4 : 3 * BS * 4);
+      return true;
     }
     c -= 3;
     if (fwd) {
       constexpr int NBLK = HALO ? (XI ? 2 : 1) : 0;
       if (c < NBLK) {
         const float* arr = XI ? (c == 0 ? pd.AQ : pd.QAt) : pd.Om;
-        *src = arr + (size_t)(i * N + j0) * 80;
-        *dst = &B.blk[c * 160];
-        return (two_cols ? 2u : 1u) * 320u;
+        d.base = reinterpret_cast<const char*>(arr + (size_t)j0 * 80);
+        d.stride8 = (unsigned)(N * 40);
+        d.dst = buf_off(&B.blk[c * 160]);
+        d.info = (unsigned short)((two_cols ? 2u : 1u) * 320u);
+        return true;
       }
       c -= NBLK;
       if (HALO) {
         if (c < 8) {
-          if (!((row_valid(i) >> c) & 1u)) return 0u;
+          if (!((col_ok >> c) & 1u)) return false;
           const unsigned code = (unsigned)((packed >> (5 * c)) & 31ull);
           const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
           const int ta = XI ? (tl - 1 > 0 ? tl - 1 : 0) : tl;
           const int tb = XI ? (th + 1 < T ? th + 1 : T) : th;
-          *src = hvec + ((long long)((i + di) * N + jn) * Tp + ta) * NS;
-          *dst = &B.halo[c][ta - (tl - 1)][0];
-          return (unsigned)(tb - ta + 1) * 16u;
+          d.base = reinterpret_cast<const char*>(hvec) + ((long long)(di * N + jn) * Tp + ta) * NS * 4;
+          d.stride8 = row_iter8;
+          d.dst = buf_off(&B.halo[c][ta - (tl - 1)][0]);
+          d.info = (unsigned short)((tb - ta + 1) * 16) | (di < 0 ? kNeedAbove : 0) | (di > 0 ? kNeedBelow : 0);
+          return true;
         }
         c -= 8;
       }
       if (src32g != nullptr) {
-        if (c < 2) {
-          if (c == 1 && !two_cols) return 0u;
-          *src = src32g + ((long long)(i * N + j0 + c) * Tp + tl) * NS;
-          *dst = &B.src32[c][0][0];
-          return (unsigned)ntl * 16u;
-        }
-        return 0u;
+        if (c >= 2 || (c == 1 && !two_cols)) return false;
+        d.base = reinterpret_cast<const char*>(src32g + ((long long)(j0 + c) * Tp + tl) * NS);
+        d.stride8 = row_iter8;
+        d.dst = buf_off(&B.src32[c][0][0]);
+        d.info = (unsigned short)(ntl * 16);
+        return true;
       }
       constexpr int NVF = UPDATE ? 4 : 1;
-      if (c < NVF * 8) {
-        const int vv = c >> 3, cjj = (c >> 2) & 1, kk = c & 3;
-        if (cjj == 1 && !two_cols) return 0u;
-        const double* vec = UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src;
-        *dst = &B.src64[vv][cjj][kk][0];
-        return run64(vec, i, cjj, kk, src);
-      }
-      return 0u;
+      if (c >= NVF * 8) return false;
+      const int vv = c >> 3, cjj = (c >> 2) & 1, kk = c & 3;
+      if (cjj == 1 && !two_cols) return false;
+      run64(UPDATE ? (vv == 0 ? a.r : vv == 1 ? a.y : vv == 2 ? a.d : a.delta) : a.src, cjj, kk, d);
+      d.dst = buf_off(&B.src64[vv][cjj][kk][0]);
+      return true;
     }
     // backward: the forward result y_i of the tile, then r (and y) for mu
     if (c < 2) {
-      if (c == 1 && !two_cols) return 0u;
-      *src = a.theta_out + ((long long)(i * N + j0 + c) * Tp + tl) * NS;
-      *dst = &B.src32[c][0][0];
-      return (unsigned)ntl * 16u;
+      if (c == 1 && !two_cols) return false;
+      d.base = reinterpret_cast<const char*>(a.theta_out + ((long long)(j0 + c) * Tp + tl) * NS);
+      d.stride8 = row_iter8;
+      d.dst = buf_off(&B.src32[c][0][0]);
+      d.info = (unsigned short)(ntl * 16);
+      return true;
     }
     c -= 2;
-    if (MU && c < (flex_dot ? 16 : 8)) {
-      const int vv = c >> 3, cjj = (c >> 2) & 1, kk = c & 3;
-      if (cjj == 1 && !two_cols) return 0u;
-      *dst = &B.src64[vv][cjj][kk][0];
-      return run64(vv == 0 ? a.r : a.y, i, cjj, kk, src);
+    if (!MU || c >= (flex_dot ? 16 : 8)) return false;
+    const int vv = c >> 3, cjj = (c >> 2) & 1, kk = c & 3;
+    if (cjj == 1 && !two_cols) return false;
+    run64(vv == 0 ? a.r : a.y, cjj, kk, d);
+    d.dst = buf_off(&B.src64[vv][cjj][kk][0]);
+    return true;
+  };
+  if (tid == 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      CopyDesc* out = pass == 0 ? sm.desc_f : sm.desc_b;
+      const int cap = pass == 0 ? Gm::NFWD : Gm::NBWD;
+      int nd = 0;
+      for (int c = 0; c < kMaxCopies; ++c) {
+        CopyDesc d;  // cap: the most copies a pass of this variant has (never reached past)
+        if (describe(c, pass == 0, d) && nd < cap) out[nd++] = d;
+      }
+      sm.ndesc[pass] = nd;
     }
-    return 0u;
+  }
+  __syncthreads();
+  // the thread of copy c: spread over the warps (c = lane * warps + warp),
+  // so that every warp issues about as many copies
+  auto copy_index = [&](int q) -> int {
+    if constexpr (THR >= 64) return (tid & 31) * (THR / 32) + (tid >> 5) + q * THR;
+    else return tid + q * THR;
   };
   // every thread arrives once per staged step, announcing the bytes of its copies
   auto stage = [&](int s) {
     const bool fwd = s < K;
     const int i = fwd ? s : 2 * K - 1 - s;
     const int b = s % NB;
-    const void* srcs[CPT];
-    void* dsts[CPT];
+    const int pass = fwd ? 0 : 1;
+    const int nd = sm.ndesc[pass];
+    unsigned char* dbuf = reinterpret_cast<unsigned char*>(&sm.buf[b]);
+    const char* srcs[CPT];
+    unsigned dsts[CPT];
     unsigned by[CPT];
     unsigned total = 0u;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       by[q] = 0u;
-      const int c = tid + q * THR;
-      if (c < kMaxCopies) by[q] = decode(c, i, fwd, b, &srcs[q], &dsts[q]);
-      total += by[q];
+      const int c = copy_index(q);
+      if (c < nd) {
+        const CopyDesc d = fwd ? sm.desc_f[c] : sm.desc_b[c];
+        const bool ok = !((d.info & kNeedAbove) && i < 1) && !((d.info & kNeedBelow) && i + 1 >= K);
+        if (ok) {
+          const char* src = d.base + (long long)i * d.stride8 * 8;
+          unsigned bytes = d.info & kBytesMask;
+          if (d.info & kRun64) {
+            // the run's first element may sit at an odd double: copy from the
+            // 16-byte boundary below it (the reader offsets by that parity)
+            const unsigned par = (unsigned)(reinterpret_cast<uintptr_t>(src) >> 3) & 1u;
+            src -= par * 8;
+            bytes = ((par + (unsigned)ntl + 1u) & ~1u) * 8u;
+          }
+          srcs[q] = src;
+          dsts[q] = d.dst;
+          by[q] = bytes;
+          total += bytes;
+        }
+      }
     }
     if (total) mbar_arrive_expect(&sm.bar[b], total);
     else mbar_arrive(&sm.bar[b]);
 #pragma unroll
     for (int q = 0; q < CPT; ++q)
-      if (by[q]) bulk_load(dsts[q], srcs[q], by[q], &sm.bar[b]);
+      if (by[q]) bulk_load(dbuf + dsts[q], srcs[q], by[q], &sm.bar[b]);
   };
   // a wait that ran out: record it, let the staged copies land, end the CTA
   int staged = 0;
