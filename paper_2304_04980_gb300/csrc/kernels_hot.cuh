@@ -33,6 +33,53 @@ __device__ __forceinline__ long long q_index(const Grid& g, int k, long long pt)
   else return k * g.Ps + pt;
 }
 
+// The NS components of a node-time pt of a vector in that layout (FP32
+// node-major, one 16-byte access at NS = 4; FP64 component planes).  The
+// Delta product's FP32 temporaries (z, the FP32 copy of d) use it too.
+template <int NS, typename T>
+__device__ __forceinline__ void load_iter(const Grid& g, const T* __restrict__ v, long long pt, T (&out)[NS]) {
+  if constexpr (sizeof(T) == 4 && NS == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(v + pt * 4);
+    out[0] = x.x; out[1] = x.y; out[2] = x.z; out[3] = x.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) out[k] = v[q_index<NS, T>(g, k, pt)];
+  }
+}
+template <int NS, typename T>
+__device__ __forceinline__ void store_iter(const Grid& g, T* __restrict__ v, long long pt, const T (&in)[NS]) {
+  if constexpr (sizeof(T) == 4 && NS == 4) {
+    *reinterpret_cast<float4*>(v + pt * 4) = make_float4(in[0], in[1], in[2], in[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) v[q_index<NS, T>(g, k, pt)] = in[k];
+  }
+}
+
+// An NS x NS node block (row-major) into registers, in 16-byte loads at
+// NS = 4 (every block starts at a multiple of 64 bytes).
+template <int NS, typename T>
+__device__ __forceinline__ void load_block(const T* __restrict__ b, T (&out)[NS * NS]) {
+  if constexpr (NS == 4 && sizeof(T) == 4) {
+    const float4* v = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float4 x = v[e];
+      out[4 * e] = x.x; out[4 * e + 1] = x.y; out[4 * e + 2] = x.z; out[4 * e + 3] = x.w;
+    }
+  } else if constexpr (NS == 4 && sizeof(T) == 8) {
+    const double2* v = reinterpret_cast<const double2*>(b);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const double2 x = v[e];
+      out[2 * e] = x.x; out[2 * e + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < NS * NS; ++e) out[e] = b[e];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Delta apply, part 1: z = Q~^-1 A~' dn, one thread per (node, t).
 //   (A~' dn)_t = -dn_t + A_hat' dn_{t+1}   (t < T),   (A~' dn)_T = -dn_T
@@ -58,41 +105,47 @@ __device__ __forceinline__ void delta_z_body(const Grid& g, const OpData<CT>& nd
   // when the FP32 copy of d is read)
   const DT beta = use_beta == 1 ? (DT)st->beta : DT(0);
   const bool mix = beta != DT(0);
-  CT w[NS];
+  // d_old: FP64 component planes, or the FP32 copy (node-major)
+  auto dn_at = [&](long long pt, CT (&out)[NS], bool negate) {
+    QT qv[NS];
+    load_iter<NS, QT>(g, q, pt, qv);
+    DT dv[NS];
+    if (mix) load_iter<NS, DT>(g, dold, pt, dv);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    DT dv = (DT)q[q_index<NS, QT>(g, k, idx)];
-    if (mix) dv += beta * dold[k * g.Ps + idx];
-    w[k] = (CT)(-dv);
-  }
+    for (int k = 0; k < NS; ++k) {
+      DT d = (DT)qv[k];
+      if (mix) d += beta * dv[k];
+      out[k] = negate ? (CT)(-d) : (CT)d;
+    }
+  };
+  CT w[NS];
+  dn_at(idx, w, true);
   if (t < g.T) {
 #pragma unroll
     for (int dir = 0; dir < 5; ++dir) {
       const int r = nbr_node(i, j, dir, g.K, g.N);
       if (r < 0) continue;
-      const CT* blk = ahat_col<NS>(nd, r, dir);
-      const long long ridx = (long long)r * Tp + t + 1;
+      CT blk[NS * NS];
+      load_block<NS, CT>(ahat_col<NS>(nd, r, dir), blk);
       CT dv[NS];
-#pragma unroll
-      for (int c = 0; c < NS; ++c) {
-        DT dd = (DT)q[q_index<NS, QT>(g, c, ridx)];
-        if (mix) dd += beta * dold[c * g.Ps + ridx];
-        dv[c] = (CT)dd;
-      }
+      dn_at((long long)r * Tp + t + 1, dv, false);
 #pragma unroll
       for (int c = 0; c < NS; ++c)
 #pragma unroll
         for (int k = 0; k < NS; ++k) w[k] += blk[c * NS + k] * dv[c];
     }
   }
-  const CT* Qb = (t == g.T ? nd.QTi : nd.Qi) + (size_t)p * NS * NS;
+  CT Qb[NS * NS];
+  load_block<NS, CT>((t == g.T ? nd.QTi : nd.Qi) + (size_t)p * NS * NS, Qb);
+  CT zv[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     CT s = CT(0);
 #pragma unroll
     for (int c = 0; c < NS; ++c) s += Qb[k * NS + c] * w[c];
-    z[k * g.Ps + idx] = s;
+    zv[k] = s;
   }
+  store_iter<NS, CT>(g, z, idx, zv);  // FP32 z: node-major, read only by delta_y
 }
 
 template <int NS, typename QT, typename CT, typename DT>
@@ -127,42 +180,61 @@ __device__ __forceinline__ void delta_y_body(const Grid& g, const OpData<CT>& nd
     const int i = p / g.N, j = p % g.N;
     const double beta = LOOP ? st->beta : 0.0;
     double dn[NS];
-    CT yk[NS];
+    CT dnc[NS], yk[NS];
+    {
+      QT qv[NS];
+      load_iter<NS, QT>(g, q, idx, qv);
+      double dv[NS];
+      if (LOOP && beta != 0.0) load_iter<NS, double>(g, dold, idx, dv);
+      CT zs[NS];
+      load_iter<NS, CT>(g, z, idx, zs);
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      double dv = (double)q[q_index<NS, QT>(g, k, idx)];
-      if (LOOP && beta != 0.0) dv += beta * dold[k * g.Ps + idx];
-      dn[k] = dv;
-      yk[k] = -z[k * g.Ps + idx];
+      for (int k = 0; k < NS; ++k) {
+        double d = (double)qv[k];
+        if (LOOP && beta != 0.0) d += beta * dv[k];
+        dn[k] = d;
+        dnc[k] = (CT)d;
+        yk[k] = -zs[k];
+      }
     }
     if (t >= 1) {
 #pragma unroll
       for (int dir = 0; dir < 5; ++dir) {
         const int r = nbr_node(i, j, dir, g.K, g.N);
         if (r < 0) continue;
-        const CT* blk = ahat_row<NS>(nd, p, dir);
-        const long long ridx = (long long)r * Tp + t - 1;
+        CT blk[NS * NS];
+        load_block<NS, CT>(ahat_row<NS>(nd, p, dir), blk);
         CT zv[NS];
-#pragma unroll
-        for (int c = 0; c < NS; ++c) zv[c] = z[c * g.Ps + ridx];
+        load_iter<NS, CT>(g, z, (long long)r * Tp + t - 1, zv);
 #pragma unroll
         for (int k = 0; k < NS; ++k)
 #pragma unroll
           for (int c = 0; c < NS; ++c) yk[k] += blk[k * NS + c] * zv[c];
       }
-      const CT* S = nd.Sb + (size_t)p * NS * NS;
+      CT S[NS * NS];
+      load_block<NS, CT>(nd.Sb + (size_t)p * NS * NS, S);
 #pragma unroll
       for (int k = 0; k < NS; ++k)
 #pragma unroll
-        for (int c = 0; c < NS; ++c) yk[k] += S[k * NS + c] * (CT)dn[c];
+        for (int c = 0; c < NS; ++c) yk[k] += S[k * NS + c] * dnc[c];
     }
+    CT part = CT(0);  // FP32 product: y'dn of the node-time in FP32, summed in FP64 below
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       y[k * g.Ps + idx] = (double)yk[k];
       if (LOOP) {
         dout[k * g.Ps + idx] = dn[k];
-        if (dout32 != nullptr) dout32[k * g.Ps + idx] = (float)dn[k];
-        acc += (double)yk[k] * dn[k];
+        if constexpr (sizeof(CT) == 4) part += yk[k] * dnc[k];
+        else acc += (double)yk[k] * dn[k];
+      }
+    }
+    if (LOOP && sizeof(CT) == 4) {
+      acc = (double)part;
+      if (dout32 != nullptr) {
+        float d32[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) d32[k] = (float)dnc[k];
+        store_iter<NS, float>(g, dout32, idx, d32);  // node-major, read by the next delta_z
       }
     }
   }
