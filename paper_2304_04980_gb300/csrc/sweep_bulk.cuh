@@ -24,7 +24,8 @@
 //    run, completing on the step buffer's mbarrier, instead of one cp.async
 //    per element.
 //  * Three staging buffers keep two pair-rows in flight (two buffers, one
-//    pair-row, when a lane carries four time steps).  Every wait on an
+//    pair-row, for the update and mu sweeps when a lane carries four time
+//    steps).  Every wait on an
 //    mbarrier is bounded; a wait that runs out sets the solver state to the
 //    loop-cap status and a fault word, lets the copies in flight land
 //    (again bounded) and ends the CTA.
@@ -39,12 +40,13 @@ namespace hot {
 namespace bulk {
 
 constexpr int NS = 4, G2 = 8, BS = 64, REC = 6 * BS;  // record: [N2][N1][D^-1][F2][F1][L0^-1]
-// Staging buffers: three (two pair-rows in flight) when a lane carries one or
-// two time steps; two when it carries four, whose steps are long enough to
-// cover a copy's latency with one pair-row in flight, and whose shared
-// memory then allows six CTAs per SM.
-template <int R>
-constexpr int stages() { return R >= 4 ? 2 : 3; }
+// Staging buffers: three (two pair-rows in flight), except two for the
+// sweeps that stage FP64 runs of several vectors (the PCG update, the mu
+// sweep) at four time steps per lane: their steps are long enough to cover a
+// copy's latency with one pair-row in flight, and a third buffer would cost
+// them CTAs per SM (a second wave on the 256 x 256 x 200 grid).
+template <int VAR, int R>
+constexpr int stages() { return R >= 4 && (VAR == kSweepUpdate || VAR == kSweepOmegaMu) ? 2 : 3; }
 // A wait gives up after kWaitCap rounds of try_wait, each suspending for at
 // most about kWaitHintNs: about a second in all.
 constexpr unsigned kWaitCap = 1u << 20;
@@ -162,9 +164,9 @@ struct Smem {
     float src32[2][G::HW][NS];            // forward: r_theta (FP32); backward: the forward result y_i
     double src64[G::NV][2][NS][G::RUN64]; // FP64 runs: r, y, d, delta (update); r (source); r, y (mu)
   };
-  Buf buf[stages<R>()];
+  Buf buf[stages<VAR, R>()];
   float xy[G::NG][R][G2];                 // per group: the step's result, exchanged inside the group
-  uint64_t bar[stages<R>()];
+  uint64_t bar[stages<VAR, R>()];
   CopyDesc desc_f[G::NFWD];               // the CTA's copies per step: forward pass
   CopyDesc desc_b[G::NBWD];               // backward pass
   int ndesc[2];
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(THR, (bulk::min_blocks<VAR, R, THR>()))
   constexpr bool UPDATE = Gm::UPDATE, XI = Gm::XI, OMEGA = Gm::OMEGA, MU = Gm::MU;
   constexpr bool HALO = XI || OMEGA;
   constexpr bool XIOM = VAR == kSweepXiOmega;
-  constexpr int NB = stages<R>();
+  constexpr int NB = stages<VAR, R>();
   constexpr int PD = NB - 1;
   constexpr int CPT = (kMaxCopies + THR - 1) / THR;
   extern __shared__ __align__(128) unsigned char bulk_smem[];
