@@ -639,9 +639,10 @@ def run_ours(args, dist):
         # ---- end to end: host (pinned) inputs in, host outputs back, per step
         if headline:
             pinned = [torch.from_numpy(a).pin_memory() for a in host]
-            xh = np.empty((g.T + 1, g.nodes, g.n))
-            uh = np.empty((g.T, g.nodes, g.m))
-            lh = np.empty_like(xh)
+            # the outputs land in pinned host buffers too (a user's numpy views of them)
+            outs = [torch.empty(shape, dtype=torch.float64).pin_memory()
+                    for shape in ((g.T + 1, g.nodes, g.n), (g.T, g.nodes, g.m), (g.T + 1, g.nodes, g.n))]
+            xh, uh, lh = (o.numpy() for o in outs)
             res["h2d"] = sum(a.nbytes for a in host)
             res["d2h"] = xh.nbytes + uh.nbytes + lh.nbytes
             torch.cuda.synchronize()
