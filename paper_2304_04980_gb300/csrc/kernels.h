@@ -178,6 +178,10 @@ void launch_to_f32(const double* src, float* dst, long long count, cudaStream_t 
 void launch_to_f64(const float* src, double* dst, long long count, cudaStream_t s);
 // an FP32 iterate of the preconditioner (node-major) into an FP64 vector in
 // component planes
+// d = q + beta d in FP64 (beta from the state), skipped once the state is
+// done; q FP64 (component planes) or FP32 (node-major)
+void launch_direction_update(const Grid& g, const void* q, bool q_f32, double* d, const SolverState* st,
+                             cudaStream_t s);
 void launch_iter_f32_to_f64(const Grid& g, const float* src, double* dst, cudaStream_t s);
 // records of the t = 0 factor class for the n = 4 FP32 sweeps: F = N = 0,
 // D^-1 = blkdiag(Q of the pair-row's nodes), from the FP32 copy of Q

@@ -104,7 +104,7 @@ __device__ __forceinline__ void delta_z_body(const Grid& g, const OpData<CT>& nd
   // dn = q + beta d_old is formed in the precision of d_old (FP64, or FP32
   // when the FP32 copy of d is read)
   const DT beta = use_beta == 1 ? (DT)st->beta : DT(0);
-  const bool mix = beta != DT(0);
+  const bool mix = beta != DT(0) && dold != nullptr;  // no d_old: q already holds the new direction
   // d_old: FP64 component planes, or the FP32 copy (node-major)
   auto dn_at = [&](long long pt, CT (&out)[NS], bool negate) {
     QT qv[NS];
@@ -185,13 +185,14 @@ __device__ __forceinline__ void delta_y_body(const Grid& g, const OpData<CT>& nd
       QT qv[NS];
       load_iter<NS, QT>(g, q, idx, qv);
       double dv[NS];
-      if (LOOP && beta != 0.0) load_iter<NS, double>(g, dold, idx, dv);
+      const bool mix = LOOP && beta != 0.0 && dold != nullptr;  // no d_old: q is the new direction
+      if (mix) load_iter<NS, double>(g, dold, idx, dv);
       CT zs[NS];
       load_iter<NS, CT>(g, z, idx, zs);
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         double d = (double)qv[k];
-        if (LOOP && beta != 0.0) d += beta * dv[k];
+        if (mix) d += beta * dv[k];
         dn[k] = d;
         dnc[k] = (CT)d;
         yk[k] = -zs[k];
@@ -223,7 +224,7 @@ __device__ __forceinline__ void delta_y_body(const Grid& g, const OpData<CT>& nd
     for (int k = 0; k < NS; ++k) {
       y[k * g.Ps + idx] = (double)yk[k];
       if (LOOP) {
-        dout[k * g.Ps + idx] = dn[k];
+        if (dout != nullptr) dout[k * g.Ps + idx] = dn[k];
         if constexpr (sizeof(CT) == 4) part += yk[k] * dnc[k];
         else acc += (double)yk[k] * dn[k];
       }

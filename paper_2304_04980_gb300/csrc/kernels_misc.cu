@@ -387,6 +387,31 @@ void launch_to_f64(const float* src, double* dst, long long count, cudaStream_t 
   to_f64_kernel<<<blocks_for(count, 256), 256, 0, s>>>(src, dst, count);
 }
 
+// d = q + beta d (Algorithm 1's direction update, beta from the state; d = q
+// when beta = 0), in FP64, once per node-time ahead of the Delta product,
+// which then reads d instead of forming it for each stencil neighbour.  q is
+// the preconditioner output: FP64 component planes, or FP32 node-major.
+__global__ void direction_update_kernel(Grid g, const void* __restrict__ q, int q_f32, double* __restrict__ d,
+                                        const SolverState* __restrict__ st) {
+  if (st->done) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.P) return;
+  const double beta = st->beta;
+  for (int k = 0; k < g.n; ++k) {
+    const double qv = q_f32 ? (double)static_cast<const float*>(q)[iter_f32_index(g.n, k, idx)]
+                            : static_cast<const double*>(q)[k * g.Ps + idx];
+    double* dp = d + k * g.Ps + idx;
+    double v = qv;
+    if (beta != 0.0) v += beta * *dp;
+    *dp = v;
+  }
+}
+
+void launch_direction_update(const Grid& g, const void* q, bool q_f32, double* d, const SolverState* st,
+                             cudaStream_t s) {
+  direction_update_kernel<<<(unsigned)((g.P + 255) / 256), 256, 0, s>>>(g, q, q_f32 ? 1 : 0, d, st);
+}
+
 void launch_iter_f32_to_f64(const Grid& g, const float* src, double* dst, cudaStream_t s) {
   iter_f32_to_f64_kernel<<<blocks_for(g.P, 256), 256, 0, s>>>(g, src, dst);
 }
