@@ -263,7 +263,11 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   // (slots with di < 0, di > 0) select.
   const long long row_stride = (long long)g.N * Tp;
   const unsigned long long packed = XI ? kXiPacked : kOmPacked;
-  constexpr int HALO_N = HALO ? Geo::NH * NS * HW : 0;
+  // FP32 node-major iterates at n = 4: one (node, t) is a 16-byte run, staged
+  // by one copy; otherwise one copy per element
+  constexpr bool H16 = FLEX && NS == 4;
+  constexpr int HU = H16 ? NS : 1;  // elements per halo copy
+  constexpr int HALO_N = HALO ? Geo::NH * NS * HW / HU : 0;
   constexpr int HSL = (HALO_N + THR - 1) / THR > 0 ? (HALO_N + THR - 1) / THR : 1;
   const VT* h_ptr[HSL];
   unsigned h_ok = 0u, h_up = 0u, h_dn = 0u;
@@ -273,12 +277,12 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
     for (int sl = 0; sl < HSL; ++sl) {
       // component fastest, so that consecutive threads fill consecutive
       // words of the [h][w][k] staging array
-      const int e = tid + sl * THR;
+      const int e = (tid + sl * THR) * HU;
       const int h = e / (NS * HW), w = (e / NS) % HW, kk = e % NS;
       const int tt = t0 - 1 + w;
       const unsigned code = (unsigned)((packed >> (5 * (h & 7))) & 31ull);
       const int di = (int)(code & 3u) - 1, jn = j0 + (int)(code >> 2) - 2;
-      const bool ok = e < HALO_N && tt >= 0 && tt <= g.T && jn >= 0 && jn < g.N;
+      const bool ok = tid + sl * THR < HALO_N && tt >= 0 && tt <= g.T && jn >= 0 && jn < g.N;
       // pair-row 0's address; at di = -1 it lies one grid row below the
       // plane's start and is used only from pair-row 1 on
       h_ptr[sl] = vec + (ok ? it_idx(kk, (long long)(di * g.N + jn) * Tp + tt) : 0);
@@ -423,7 +427,11 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
       const unsigned hv = h_ok & (i == 0 ? ~h_up : ~0u) & (i + 1 >= g.K ? ~h_dn : ~0u);
 #pragma unroll
       for (int sl = 0; sl < HSL; ++sl)
-        if ((hv >> sl) & 1u) cp_async_elem(&sm.halo[b][0][0][0] + tid + sl * THR, h_ptr[sl] + rb * VS);
+        if ((hv >> sl) & 1u) {
+          VT* dst = &sm.halo[b][0][0][0] + (tid + sl * THR) * HU;
+          if constexpr (H16) cp_async_16(dst, h_ptr[sl] + rb * VS);
+          else cp_async_elem(dst, h_ptr[sl] + rb * VS);
+        }
       const long long bb = (long long)i * g.N * RUN;
 #pragma unroll
       for (int sl = 0; sl < BSL; ++sl) {
