@@ -202,7 +202,9 @@ def band_solve_flops(K, n, cols):
     factor of one Phi_bar_{v,t} block (Section IV-B), envelope entries only:
     each multiply-add counts 2 flops, each diagonal scaling 1.  This is the
     algorithmic count whatever form the kernel stores the factor in; the
-    sweeps' unit-factor form (dense F2 and D^-1 blocks) executes 7-13% more."""
+    sweeps' unit-factor form (dense F2, F1, N1 and D^-1 blocks, the
+    block-diagonal coupling E in the backward step) executes as many
+    multiply-adds per interior pair-row."""
     f = 0
     for i in range(K):
         for a in range(cols * n):

@@ -269,10 +269,14 @@ __global__ void setup_omega_kernel(SetupBuffers sb, int K, int N, int n) {
 // product with the pivot, one of six 2n x 2n products per pair-row.
 // Record of pair-row i (G2 = 2n, blocks G2 x G2 row-major, so a lane's row
 // is contiguous):
-//   [N2_i][N1_i][D_i^-1]   (backward step i)
-//   [F2_i][F1_i][L0_i^-1]  (forward step i; the sweeps read F2 and F1, the
-//                           multi-right-hand-side path applies D_i^-1 as
-//                           L0_i^-T L0_i^-1 in TF32)
+//   [N2_i][N1_i][D_i^-1][E_i]  (backward step i; E_i = A_{i,i+2}, the block of
+//                               Phi_bar coupling the pair-row to the one two
+//                               rows on, so that N2_i = D_i^-1 E_i: the tiled
+//                               sweeps form x_i = D_i^-1 (y_i - E_i x_{i+2})
+//                               - N1_i x_{i+1}, E_i being block diagonal)
+//   [F2_i][F1_i][L0_i^-1]      (forward step i; the sweeps read F2 and F1, the
+//                               multi-right-hand-side path applies D_i^-1 as
+//                               L0_i^-T L0_i^-1 in TF32)
 //
 // rev = 1 runs the same recurrences over the pair-rows in reverse order
 // (step i factors physical pair-row K-1-i, whose "previous" rows are the ones
@@ -353,6 +357,11 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       tmp[e] = s;
     }
     __syncwarp();
+    // --- E of the record two pair-rows back: A_{i-2,i} = A_{i,i-2}'
+    if (i >= 2) {
+      double* rp = out + (size_t)vc * fac_vc + (size_t)(i - 2) * fac_rec;
+      for (int e = lane; e < BS; e += 32) rp[3 * BS + e] = Aim2[(e % G2) * G2 + e / G2];
+    }
     // --- L1 = tmp L0_{i-1}^-T
     for (int e = lane; e < BS; e += 32) {
       const int a = e / G2, b = e % G2;
@@ -453,8 +462,8 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       }
     }
     __syncwarp();
-    // --- record of pair-row i: the backward blocks N2_i, N1_i start at
-    //     zero and are filled by the next two pair-rows
+    // --- record of pair-row i: the backward blocks N2_i, N1_i, E_i start
+    //     at zero and are filled by the next two pair-rows
     double* rec = rec_base + (size_t)i * fac_rec;
     for (int e = lane; e < BS; e += 32) {
       const int a = e / G2, b = e % G2;
@@ -464,9 +473,10 @@ __global__ void setup_factor_kernel(SetupBuffers sb, int K, int N, int n, int V,
       rec[0 * BS + e] = 0.0;
       rec[1 * BS + e] = 0.0;
       rec[2 * BS + e] = dinv;
-      rec[3 * BS + e] = F2[e];
-      rec[4 * BS + e] = F1[e];
-      rec[5 * BS + e] = L0i[e];
+      rec[3 * BS + e] = 0.0;
+      rec[4 * BS + e] = F2[e];
+      rec[5 * BS + e] = F1[e];
+      rec[6 * BS + e] = L0i[e];
       prevL1[e] = L1[e];
     }
     __syncwarp();

@@ -247,7 +247,7 @@ int allocate(lq2d_problem* h, int K, int N, int T, int n, int m) {
   ALLOC(sb.QAt, NN * 5 * nn);
   ALLOC(sb.M13, NN * 13 * nn);
   ALLOC(sb.Om, NN * 5 * nn);
-  const long long fac_rec = 24LL * n * n;
+  const long long fac_rec = 28LL * n * n;  // 7 blocks of (2n)^2: [N2][N1][D^-1][E][F2][F1][L0^-1]
   const long long fac_vc = fac_rec * K;
   ALLOC(sb.fac, (size_t)g.V * 2 * fac_vc);
   if (n == 4 && K >= kTwistedMinK) {

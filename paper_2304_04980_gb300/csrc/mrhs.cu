@@ -418,10 +418,12 @@ __global__ void mrhs_records_kernel(Grid g, NodeData nd, float* rec) {
       const int row = gq, col = q + 4 * k2;
       double val = 0.0;
       if (cls < 2) {
-        const double* blk = nd.fac + (size_t)(2 * v + cls) * nd.fac_vc + (size_t)i * nd.fac_rec + bk * 64;
-        // block 2 is L0^-T, the transpose of block 5 (the record's D^-1
-        // serves the single-RHS sweep)
-        val = bk == 2 ? blk[3 * 64 + col * 8 + row] : blk[row * 8 + col];
+        // source slots of the FP64 record [N2][N1][D^-1][E][F2][F1][L0^-1]:
+        // block 2 is L0^-T, the transpose of L0^-1 (the record's D^-1
+        // serves the single-RHS sweeps)
+        const int slot = bk == 0 ? 0 : bk == 1 ? 1 : bk == 3 ? 4 : bk == 4 ? 5 : 6;
+        const double* blk = nd.fac + (size_t)(2 * v + cls) * nd.fac_vc + (size_t)i * nd.fac_rec + slot * 64;
+        val = bk == 2 ? blk[col * 8 + row] : blk[row * 8 + col];
         if (bk == 0 || bk == 1 || bk == 3 || bk == 4) val = -val;
       } else if (bk == 2) {
         val = row == col ? 1.0 : 0.0;

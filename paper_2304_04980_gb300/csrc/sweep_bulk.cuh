@@ -39,7 +39,7 @@ namespace lq2d {
 namespace hot {
 namespace bulk {
 
-constexpr int NS = 4, G2 = 8, BS = 64, REC = 6 * BS;  // record: [N2][N1][D^-1][F2][F1][L0^-1]
+constexpr int NS = 4, G2 = 8, BS = 64, REC = 7 * BS;  // record: [N2][N1][D^-1][E][F2][F1][L0^-1]
 // Staging buffers: three (two pair-rows in flight), except two for the
 // sweeps that stage FP64 runs of several vectors (the PCG update, the mu
 // sweep) at four time steps per lane: their steps are long enough to cover a
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(THR, (bulk::min_blocks<VAR, R, THR>()))
     if (c < 3) {
       if (!((cls_mask >> c) & 1u)) return false;
       const float* f = c == 2 ? pd.fac_t0 + (size_t)v * pd.fac_vc : pd.fac + (size_t)(2 * v + c) * pd.fac_vc;
-      d.base = reinterpret_cast<const char*>(f + (fwd ? 3 * BS : 0));
+      d.base = reinterpret_cast<const char*>(f + (fwd ? 4 * BS : 0));  // [F2][F1] or [N2][N1][D^-1]
       d.stride8 = (unsigned)(pd.fac_rec / 2);
       d.dst = buf_off(&B.fac[c][0]);
       d.info = (unsigned short)(fwd ? 2 * BS * 4 : 3 * BS * 4);

@@ -18,16 +18,17 @@
 //   * the Omega~ / Xi~ node blocks of the pair-row's two nodes.
 // Per pair-row i, with the block Cholesky factor split at setup into a unit
 // block factor F and the pivots D (Phi_bar = F D F'; N1_i = F1_{i+1}',
-// N2_i = F2_{i+2}'):
+// N2_i = F2_{i+2}' = D_i^-1 E_i with E_i = A_{i,i+2}, the block of Phi_bar
+// coupling pair-row i to pair-row i+2, which is block diagonal):
 //   forward:  y_i = tau_i - F2_i y_{i-2} - F1_i y_{i-1}
-//   backward: x_i = D_i^-1 y_i - N2_i x_{i+2} - N1_i x_{i+1}
+//   backward: x_i = D_i^-1 (y_i - E_i x_{i+2}) - N1_i x_{i+1}
 // Each lane computes one row of every block product, from row-major blocks,
 // so a lane's operands are contiguous in shared memory.  Only the last
 // product of a step waits for the previous pair-row's result, which keeps
 // the dependent chain of a step at 2n multiply-adds.  The forward step
 // starts from the lane's own entry of tau; the backward step needs all 2n
-// values of y, and the group exchanges them, and each step's result,
-// through shared memory.  y is kept in theta_out between the two passes.
+// values of y - E x_{i+2}, and the group exchanges them, and each step's
+// result, through shared memory.  y is kept in theta_out between the two passes.
 // At t = 0, Phi_bar = Q^-1 node by node, so theta = Q tau.
 #pragma once
 
@@ -332,8 +333,8 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
     s_ptr[sl] = ok ? base + kk * g.Ps + (long long)(j0 + cjj) * Tp + tt : nullptr;
     if (ok) s_ok |= 1u << sl;
   }
-  // factor blocks, 16-byte chunks: forward F2, F1 (record blocks 3..4),
-  // backward N2, N1, D^-1 (blocks 0..2), per class present in the tile
+  // factor blocks, 16-byte chunks: forward F2, F1 (record blocks 4..5),
+  // backward N1, D^-1, E (blocks 1..3), per class present in the tile
   constexpr int FSL = (2 * 2 * BS + THR * CH - 1) / (THR * CH);
   constexpr int FSLB = (2 * 3 * BS + THR * CH - 1) / (THR * CH);
   const VT* f_ptr[FSL];
@@ -343,7 +344,7 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
   for (int sl = 0; sl < FSL; ++sl) {
     const int e = (tid + sl * THR) * CH;
     const int c = e / (2 * BS), off = e % (2 * BS);
-    f_ptr[sl] = fac_pair + (size_t)c * pd.fac_vc + 3 * BS + off;
+    f_ptr[sl] = fac_pair + (size_t)c * pd.fac_vc + 4 * BS + off;
     f_sm[sl] = c * 3 * BS + off;
     if (e < ncls * 2 * BS) f_ok |= 1u << sl;
   }
@@ -352,7 +353,7 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
 #pragma unroll
   for (int sl = 0; sl < FSLB; ++sl) {
     const int e = (tid + sl * THR) * CH;  // also the shared-memory place
-    fb_ptr[sl] = fac_pair + (size_t)(e / (3 * BS)) * pd.fac_vc + e % (3 * BS);
+    fb_ptr[sl] = fac_pair + (size_t)(e / (3 * BS)) * pd.fac_vc + BS + e % (3 * BS);
     if (e < ncls * 3 * BS) fb_ok |= 1u << sl;
   }
   // backward pass: the forward result y_i of the tile (kept in theta_out
@@ -442,7 +443,7 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
     }
   };
 
-  // ---- staging of the backward step for pair-row i: N2, N1 and D^-1 of
+  // ---- staging of the backward step for pair-row i: N1, D^-1 and E of
   // pair-row i, y_i of the tile and, in the mu sweep, r (and y)
   auto stage_backward = [&](int step, int b) {
     const int i = row_b(step);
@@ -607,7 +608,7 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
     // row k; bottom: H, the forward factor's F2 of row k+1) and of S^-1
     const VT* Cm = half ? pd.fac + (size_t)(2 * v + cls) * pd.fac_vc + (size_t)(kI + 1) * pd.fac_rec
                         : pd.fac_rev + (size_t)(2 * v + cls) * pd.fac_vc + (size_t)(K - kI - 1) * pd.fac_rec;
-    Cm += 3 * BS + ac * G2;
+    Cm += 4 * BS + ac * G2;
     const VT* Srow = pd.sinv + (size_t)(2 * v + cls) * 4 * BS + (half * G2 + ac) * 2 * G2;
     if (active && al == 0) {
 #pragma unroll
@@ -677,25 +678,28 @@ __device__ __forceinline__ void nbjm_sweep_body(const Grid& g, const PrecData<VT
       }
     }
     if (t >= 1) {
-      // x_i = D^-1 y_i - N2 x_{i+2} - N1 x_{i+1}
-      const VT* rec = sm.fac[b][my_slot];  // [N2][N1][D^-1], row-major
-      if (lane_ok) sm.xw[grp][al] = yown;
+      // x_i = D^-1 (y_i - E x_{i+2}) - N1 x_{i+1}  (= D^-1 y_i - N2 x_{i+2} -
+      // N1 x_{i+1} with N2 = D^-1 E; E is block diagonal, so the lane's row
+      // of it meets only its own node's n components of x_{i+2})
+      const VT* rec = sm.fac[b][my_slot];  // [N1][D^-1][E], row-major
+      VT vown = yown;
+      if (TW || i + 2 < g.K) {
+        VT erow[NS];
+        lds_run<VT, NS>(rec + 2 * BS + ac * G2 + jj * NS, erow);
+#pragma unroll
+        for (int c = 0; c < NS; ++c) vown -= erow[c] * (jj ? xp2[NS + c] : xp2[c]);
+      }
+      if (lane_ok) sm.xw[grp][al] = vown;
       __syncwarp(gmask);
-      VT yall[G2], row0[G2];
-      lds_run<VT, G2>(&sm.xw[grp][0], yall);
-      lds_run<VT, G2>(rec + 2 * BS + ac * G2, row0);
+      VT vall[G2], row0[G2];
+      lds_run<VT, G2>(&sm.xw[grp][0], vall);
+      lds_run<VT, G2>(rec + BS + ac * G2, row0);
       VT xv = VT(0);
 #pragma unroll
-      for (int bb = 0; bb < G2; ++bb) xv += row0[bb] * yall[bb];
-      if (TW || i + 2 < g.K) {
-        VT row[G2];
-        lds_run<VT, G2>(rec + ac * G2, row);
-#pragma unroll
-        for (int bb = 0; bb < G2; ++bb) xv -= row[bb] * xp2[bb];
-      }
+      for (int bb = 0; bb < G2; ++bb) xv += row0[bb] * vall[bb];
       if (TW || i + 1 < g.K) {
         VT row[G2];
-        lds_run<VT, G2>(rec + BS + ac * G2, row);
+        lds_run<VT, G2>(rec + ac * G2, row);
 #pragma unroll
         for (int bb = 0; bb < G2; ++bb) xv -= row[bb] * xp1[bb];
       }
