@@ -525,15 +525,18 @@ __global__ void __launch_bounds__(THR, (bulk::min_blocks<VAR, R, THR>()))
     const float f1[8] = {f1a.x, f1a.y, f1a.z, f1a.w, f1b.x, f1b.y, f1b.z, f1b.w};
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float yv = tau[r];
+      // two independent sums (F2 y_{i-2} onto tau, F1 y_{i-1} from zero)
+      // halve the dependent chain of the step
+      float yv = tau[r], y1 = 0.f;
       if (i >= 2) {
 #pragma unroll
         for (int bb = 0; bb < G2; ++bb) yv = fmaf(-f2[bb], ym2[bb][r], yv);
       }
       if (i >= 1) {
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) yv = fmaf(-f1[bb], ym1[bb][r], yv);
+        for (int bb = 0; bb < G2; ++bb) y1 = fmaf(f1[bb], ym1[bb][r], y1);
       }
+      yv -= y1;
       if (node_ok && r < sp.count) a.theta_out[(prow + tr[r]) * NS + k] = yv;
       sm.xy[grp][r][al] = yv;
     }
@@ -581,17 +584,19 @@ __global__ void __launch_bounds__(THR, (bulk::min_blocks<VAR, R, THR>()))
       const int w = tr[r] - tl;
       const float4 y0 = lds4(&B.src32[0][w][0]), y1 = lds4(&B.src32[1][w][0]);
       const float yall[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-      float xv = 0.f;
+      // three independent sums, so the step's dependent chain is 2n long
+      float xv = 0.f, x2 = 0.f, x1 = 0.f;
 #pragma unroll
       for (int bb = 0; bb < G2; ++bb) xv = fmaf(dv[bb], yall[bb], xv);
       if (i + 2 < K) {
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) xv = fmaf(-n2[bb], xp2[bb][r], xv);
+        for (int bb = 0; bb < G2; ++bb) x2 = fmaf(n2[bb], xp2[bb][r], x2);
       }
       if (i + 1 < K) {
 #pragma unroll
-        for (int bb = 0; bb < G2; ++bb) xv = fmaf(-n1[bb], xp1[bb][r], xv);
+        for (int bb = 0; bb < G2; ++bb) x1 = fmaf(n1[bb], xp1[bb][r], x1);
       }
+      xv = xv - x2 - x1;
       if (node_ok && r < sp.count) {
         a.theta_out[(prow + tr[r]) * NS + k] = xv;
         if (MU) {
